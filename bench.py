@@ -1,0 +1,319 @@
+"""Throughput of the Hawkes log-likelihood + gradient on one GB300.
+
+A step is one pass of the evaluation an MCMC iteration makes: the
+cut-posterior location resample (Sec. 2.2) followed by the full FP32
+log-likelihood and six-component gradient (eq. 4) over all N(N-1)/2
+unordered event pairs, on the N = 1,000,000 synthetic Voronoi-county
+workload (3,143 counties on a 4,500 x 2,800 km box, lognormal densities,
+Hawkes-burst times over 1,200 days).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  ``value`` is unordered pairs per second over all ranks
+(each rank runs its own chain replica: weak scaling, no collective on the
+data path).  ``--impl reference`` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "loglik+grad pairs/s at N=1M (1 and 30-chain batch); HMC ESS/s surrogate vs exact"
+UNIT = "pairs/s"
+WORKLOAD = "c3: N=1,000,000 events, 1,200 d, 3,143 Voronoi counties (4,500x2,800 km), resample + FP32 loglik + 6-dim grad per step"
+# Algorithmic FP32 pipe operations per unordered pair (one lane op each:
+# FADD, FMUL or FFMA), excluding the two-word coordinate split; see the design doc.
+ALG_FP32_OPS_PER_PAIR = 19
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("sweep.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2407_11349_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """Per-launch DRAM bytes of the sweep from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "sweep_f32_c3.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    want = source_hash()
+    val, src = None, None
+    for line in txt.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            val = float(line.split(":", 1)[1].split()[0])
+        if line.startswith("kernel_source_hash:"):
+            src = line.split(":", 1)[1].strip()
+    return val if (val is not None and src == want) else None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(ds, seconds=15.0):
+    """The FP64 oracle on the host cores, on a bounded contiguous row window in
+    the middle of the workload (every row against all N sources)."""
+    import oracle
+    threads = oracle.max_threads()
+    n = ds.n
+    x, y, s = ds.x, ds.y, ds.s
+    p = ds.params
+    mid = n // 2
+    m = max(threads, 16)
+    t0 = time.perf_counter()
+    oracle.loglik_grad(ds.t, x, y, p, s=s, row_begin=mid, row_end=mid + m, threads=threads)
+    dt = time.perf_counter() - t0
+    m = int(min(n - mid, max(m, m * seconds / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.loglik_grad(ds.t, x, y, p, s=s, row_begin=mid, row_end=mid + m, threads=threads)
+    dt = time.perf_counter() - t0
+    # m rows x (n - 1) sources = m (n - 1) / 2 unordered-pair equivalents of the full sum
+    value = m * (n - 1) / 2 / dt
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"rows [{mid}, {mid + m}) of the N={n} workload, each against all sources "
+                      f"({m * (n - 1):.3g} ordered pairs in {dt:.1f} s); scaled as m(N-1)/2 pairs"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on bounded samples of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2407_11349_gb300 import synth
+    import oracle
+    ds = synth.config_dataset("c3")
+    threads = oracle.max_threads()
+    n, mid = ds.n, ds.n // 2
+    # size each step so the whole run stays within a few minutes
+    m = max(threads, 16)
+    t0 = time.perf_counter()
+    oracle.loglik_grad(ds.t, ds.x, ds.y, ds.params, s=ds.s, row_begin=mid, row_end=mid + m, threads=threads)
+    per_row = (time.perf_counter() - t0) / m
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    m = int(max(threads, min(n - mid, budget / per_row)))
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.loglik_grad(ds.t, ds.x, ds.y, ds.params, s=ds.s, row_begin=mid, row_end=mid + m,
+                           threads=threads)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    T = sum(times)
+    value = args.steps * m * (n - 1) / 2 / T
+    sample = (f"per step rows [{mid}, {mid + m}) of the N={n} workload against all sources, "
+              f"scaled as m(N-1)/2 pairs")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "oracle_sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2407_11349_gb300 import synth
+    from paper_2407_11349_gb300.hawkes import HAWKES_F32, Hawkes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    ds = synth.config_dataset("c3")
+    n = ds.n
+    pairs = n * (n - 1) / 2
+    stream = torch.cuda.current_stream()
+    hk = Hawkes(local, stream.cuda_stream)
+    hk.load(ds)
+    p = ds.params
+    chain = rank  # each rank is an independent chain replica
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+
+    def step(k):
+        hk.resample(2, chain, k)
+        return hk.loglik_grad(p, HAWKES_F32)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    hk.profile(True)
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            ll, g = step(args.warmup + k)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    prof = hk.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    T = sum(step_ms) / 1000.0
+    if world > 1:
+        t = torch.tensor([T], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T = float(t.item())
+    value = world * args.steps * pairs / T
+
+    sweep_launches, sweep_ms = prof["sweep"]
+    sweep_avg_s = sweep_ms / max(sweep_launches, 1) / 1000.0
+    pk, pk_src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_ops = sms * FP32_LANES_PER_SM * sm_mhz * 1e6
+    achieved_ops = ALG_FP32_OPS_PER_PAIR * pairs / sweep_avg_s
+    launches = sum(v[0] for v in prof.values())
+
+    # end to end through the C ABI from pinned host buffers, every step
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
+           for k, v in (("t", ds.t), ("x", ds.x), ("y", ds.y), ("county", ds.county.astype(np.int32)),
+                        ("scale", ds.county_scale))}
+    h2d = sum(v.nbytes for v in pin.values()) + 48
+    d2h = 7 * 8
+    hk.set_events(pin["t"], pin["county"], pin["scale"], pin["x"], pin["y"])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        hk.set_events(pin["t"], pin["county"], pin["scale"], pin["x"], pin["y"])
+        hk.resample(2, chain, 1000 + k)
+        ll_e, g_e = hk.loglik_grad(p, HAWKES_F32)
+    torch.cuda.synchronize()
+    Te = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([Te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        Te = float(t.item())
+    e2e_value = world * args.e2e_steps * pairs / Te
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_events": n, "pairs_per_step": pairs,
+                       "chains": world, "l2": "256 MB buffer written between timed steps",
+                       "loglik": ll, "grad": list(map(float, g))},
+            "gpu_launches": int(launches),
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
+            "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "Top/s", "frac": achieved_ops / peak_ops,
+                         "traffic": profiled_traffic(),
+                         "kernel": "k_sweep<true> (FP32 pair sweep)",
+                         "per_unit": f"{ALG_FP32_OPS_PER_PAIR} FP32 lane ops per unordered pair",
+                         "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
+                                        f"(sm_max_mhz, {pk_src})",
+                         "launch_ms": 1000 * sweep_avg_s},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(ds)
+        print(json.dumps(out))
+    hk.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

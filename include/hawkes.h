@@ -1,0 +1,189 @@
+/*
+ * libhawkes: spatiotemporal Hawkes log-likelihood, gradient and cut-posterior
+ * location resample on one NVIDIA GB300 (sm_103a).
+ *
+ * Model (Sec. 2.1, eqs. 2-4 of "Scaling Hawkes processes to one million
+ * COVID-19 cases"), for events (t_i, x_i, y_i) sorted by time:
+ *   lambda_i = max( sum_{j: t_j != t_i} mu phi2(r_ij; tau_x) phi1(t_i - t_j; tau_t)
+ *                 + sum_{j: t_j < t_i} theta omega e^{-omega (t_i - t_j)} phi2(r_ij; h s_j),
+ *                   1e-40 )
+ *   Lambda_i = mu [Phi((t_N - t_i)/tau_t) - Phi(-t_i/tau_t)] + theta [1 - e^{-omega (t_N - t_i)}]
+ *   ell      = sum_i ( log lambda_i - Lambda_i )
+ * phi2 is the 2-D spherical Gaussian density, phi1 the 1-D Gaussian density,
+ * Phi the standard normal CDF, t_N the largest event time and s_j the fixed
+ * bandwidth scale of the source event's county (eq. 3; s_j = 1 gives eq. 2).
+ * The 1e-40 floor is the clip of Sec. 2.3.1; a clipped row contributes
+ * log(1e-40) and nothing to the gradient.  The gradient is the exact
+ * derivative of ell with respect to (mu, tau_x, tau_t, theta, omega, h).
+ *
+ * Conventions
+ *  - Every call returns a status (HAWKES_OK = 0 or a negative error code);
+ *    no C++ exception crosses this interface.
+ *  - The caller owns every pointer it passes.  Host arrays are copied before
+ *    the call returns.  Device pointers (the *_async calls) must stay valid
+ *    until the work queued on the context's stream has finished.
+ *  - Units are the caller's (the test workloads use km and days); times must
+ *    be > 0 and non-decreasing, every value finite.
+ *  - A device-side failure (a bounded wait that gave up, a non-finite result)
+ *    is latched in the context and returned by the next synchronous call.
+ *  - One context is used by one host thread at a time.
+ */
+#ifndef HAWKES_H
+#define HAWKES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hawkes_ctx hawkes_ctx;
+
+/* Model parameters.  tau_x, tau_t, omega, h > 0; mu, theta >= 0. */
+typedef struct {
+    double mu;     /* background weight (mu_0) */
+    double tau_x;  /* background spatial lengthscale */
+    double tau_t;  /* background temporal lengthscale */
+    double theta;  /* self-excitation weight (xi_0) */
+    double omega;  /* excitation decay rate (1 / sigma_t) */
+    double h;      /* excitation spatial bandwidth multiplier (sigma_x) */
+} hawkes_params;
+
+enum {
+    HAWKES_OK = 0,
+    HAWKES_ERR_ARG = -1,        /* bad argument: null pointer, size, range, value */
+    HAWKES_ERR_UNSORTED = -2,   /* times not non-decreasing, or not > 0 */
+    HAWKES_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    HAWKES_ERR_NONFINITE = -4,  /* a result was NaN or infinite */
+    HAWKES_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
+    HAWKES_ERR_OOM = -6,        /* device allocation failed */
+    HAWKES_ERR_STATE = -7       /* call out of order (e.g. no events set) */
+};
+
+/* Flags for the log-likelihood calls. */
+enum {
+    HAWKES_F32 = 0,      /* pair terms in FP32 (SFU exp2), per-row and global sums in FP64 */
+    HAWKES_F64 = 1,      /* every pair term in FP64 (slow on GB300: reference path) */
+    HAWKES_MODEL2 = 0,   /* source bandwidth h * s_j from the county scale (eq. 3) */
+    HAWKES_MODEL1 = 2    /* s_j = 1 for every event (eq. 2) */
+};
+
+/* Human-readable name of a status code (static storage). */
+const char* hawkes_strerror(int status);
+
+/*
+ * Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * on that device on which all work is queued, or NULL for a stream the
+ * context creates and owns.  *out is set to NULL on failure.
+ */
+int hawkes_create(hawkes_ctx** out, int device, void* cuda_stream);
+
+/* Free the context and its device memory (waits for queued work).  NULL is a no-op. */
+void hawkes_destroy(hawkes_ctx* ctx);
+
+/*
+ * Load n events (n >= 1), replacing any previous set.
+ *   t[n]             event times, > 0, non-decreasing (HAWKES_ERR_UNSORTED otherwise)
+ *   x[n], y[n]       event locations, or both NULL (all zero until the first
+ *                    hawkes_resample_locations)
+ *   county[n]        county of each event, 0 <= county < n_counties
+ *   county_scale[n_counties]  s_c > 0, the source bandwidth scale of eq. 3
+ * Ties in t are allowed: tied events exchange neither background nor
+ * excitation terms (indicators t_j != t_i and t_j < t_i of eqs. 2-3).
+ */
+int hawkes_set_events(hawkes_ctx* ctx, int64_t n, const double* t, const double* x,
+                      const double* y, const int32_t* county, int32_t n_counties,
+                      const double* county_scale);
+
+/*
+ * County polygons for the location resample, as triangles (a fan of each
+ * convex polygon or any other partition).
+ *   tri_county[n_tri]  county of each triangle, non-decreasing; every county
+ *                      of hawkes_set_events needs triangles of positive total area
+ *   tri_xy[6 n_tri]    vertices ax, ay, bx, by, cx, cy of each triangle
+ */
+int hawkes_set_counties(hawkes_ctx* ctx, int32_t n_tri, const int32_t* tri_county,
+                        const double* tri_xy);
+
+/*
+ * Cut-posterior step of Sec. 2.2: draw every event location uniformly in its
+ * county, replacing the current locations.  Event i uses the Philox4x64-10
+ * block with counter (i, iteration, 0, 0) and key (seed, stream): word 0
+ * picks the county's triangle with probability proportional to area, words
+ * 1-2 place a uniform point in it (square-root barycentric map).  The draw
+ * is a pure function of (seed, stream, iteration, i, county) and is
+ * bit-identical to the documented FP64 formula.  Queued on the context
+ * stream; returns without waiting.
+ */
+int hawkes_resample_locations(hawkes_ctx* ctx, uint64_t seed, uint64_t stream,
+                              uint64_t iteration);
+
+/* Copy the current event locations to host arrays x[n], y[n] (synchronous). */
+int hawkes_get_locations(hawkes_ctx* ctx, double* x, double* y);
+
+/*
+ * Log-likelihood and gradient over the rows [row_begin, row_end) (the row
+ * window of Sec. 2.3.2's multi-GPU split: summing the windows of a partition
+ * of [0, n) gives the whole; every window uses all n events as sources and
+ * the global t_N).  Pass row_begin = 0, row_end = n for the whole sum.
+ *   params     host pointer
+ *   flags      HAWKES_F32 or HAWKES_F64, | HAWKES_MODEL1 for s_j = 1
+ *   loglik     host pointer to one double (ell)
+ *   grad       host pointer to six doubles, d ell / d (mu, tau_x, tau_t, theta, omega, h)
+ * Synchronous: returns after the result is on the host.
+ */
+int hawkes_loglik_grad(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags,
+                       int64_t row_begin, int64_t row_end, double* loglik, double* grad);
+
+/*
+ * As hawkes_loglik_grad over all rows, but queued on the context stream
+ * without host synchronisation, so it can be captured in a CUDA graph.
+ *   d_params  device pointer to one hawkes_params (read when the work runs)
+ *   d_out     device pointer to 7 doubles: ell, then the six partials
+ * Errors detected on the device are latched in the context.
+ */
+int hawkes_loglik_grad_async(hawkes_ctx* ctx, const hawkes_params* d_params, uint32_t flags,
+                             double* d_out);
+
+/*
+ * Per-row values for testing at full size: as hawkes_loglik_grad over all
+ * rows, and also writes rows[9 n] (host) = for each row i: ell_i, the six
+ * partials of ell_i, log lambda_i, Lambda_i.
+ */
+int hawkes_loglik_rows(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags,
+                       double* out7, double* rows);
+
+/* Timing of the context's kernels, accumulated while profiling is on. */
+typedef struct {
+    int64_t launches[8];   /* per kernel class (HAWKES_K_*) */
+    double ms[8];          /* summed CUDA-event time of those launches */
+} hawkes_profile;
+
+enum {
+    HAWKES_K_PREP = 0,     /* per-call FP32 staging of the event table */
+    HAWKES_K_SWEEP = 1,    /* FP32 pair sweep */
+    HAWKES_K_ROWS64 = 2,   /* FP64 pair rows */
+    HAWKES_K_FINAL = 3,    /* per-row finalisation + block reduction */
+    HAWKES_K_REDUCE = 4,   /* global reduction */
+    HAWKES_K_RESAMPLE = 5, /* location resample */
+    HAWKES_K_OTHER = 6     /* set-up kernels */
+};
+
+/*
+ * Turn per-kernel CUDA-event timing on (1) or off (0); turning it on clears
+ * the counters.  While on, every launch is bracketed by events on the
+ * context stream (a small overhead); not for use under graph capture.
+ */
+int hawkes_profile_enable(hawkes_ctx* ctx, int on);
+
+/* Wait for queued work and read the counters. */
+int hawkes_profile_read(hawkes_ctx* ctx, hawkes_profile* out);
+
+/* Number of events n of the current set (0 if none). */
+int64_t hawkes_num_events(const hawkes_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HAWKES_H */

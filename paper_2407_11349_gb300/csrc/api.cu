@@ -1,0 +1,466 @@
+// C-ABI entry points of libhawkes (declared in include/hawkes.h): context and
+// buffer management, argument checks, and the launch sequence of each call.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace hk {
+// kernels.cu
+__global__ void k_setup(double*, double*, double*, const int32_t*, int32_t, const double*, int64_t,
+                        int64_t, int, double*, int32_t*, int32_t*, double*, int*);
+__global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
+                       const hawkes_params*, int, int, int64_t, int64_t, Ev*, double*, double*,
+                       int*, double*);
+__global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
+                           int, int*, int*, double*, double*);
+__global__ void k_rows64(const double*, const double*, const double*, const double*,
+                         const int32_t*, const int32_t*, const double*, int, int64_t, int64_t,
+                         int64_t, int64_t, int, const int*, int*, double*, double*, double*);
+__global__ void k_reduce(const double*, int, const double*, const double*, double*, int*);
+__global__ void k_tri_area(const double*, int32_t, double*);
+__global__ void k_tri_county(const int32_t*, int32_t, int32_t, double*, int32_t*, int32_t*, int*);
+__global__ void k_tri_check(const int32_t*, int32_t, int32_t, int*);
+__global__ void k_resample(const int32_t*, int64_t, const double*, const double*, const int32_t*,
+                           const int32_t*, uint64_t, uint64_t, uint64_t, double*, double*);
+// sweep.cu
+cudaError_t sweep_setup_attributes();
+int sweep_blocks_per_sm();
+cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end);
+}  // namespace hk
+
+using namespace hk;
+
+namespace {
+
+// Restores the caller's current device when a call returns.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? HAWKES_ERR_OOM : HAWKES_ERR_CUDA;
+    }
+    return HAWKES_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? HAWKES_OK : HAWKES_ERR_CUDA; }
+
+#define HK_TRY(expr)                  \
+    do {                              \
+        int _rc = (expr);             \
+        if (_rc != HAWKES_OK) return _rc; \
+    } while (0)
+#define HK_CUDA(expr) HK_TRY(cuda_status(expr))
+
+// Run `launch` (which enqueues one kernel on c->stream); when profiling, time
+// it with a pair of events and add it to kernel class `kind`.
+template <typename F>
+int timed(hawkes_ctx* c, int kind, F launch) {
+    if (c->prof) HK_CUDA(cudaEventRecord(c->pev[0], c->stream));
+    launch();
+    HK_CUDA(cudaGetLastError());
+    if (c->prof) {
+        HK_CUDA(cudaEventRecord(c->pev[1], c->stream));
+        HK_CUDA(cudaEventSynchronize(c->pev[1]));
+        float ms = 0.f;
+        HK_CUDA(cudaEventElapsedTime(&ms, c->pev[0], c->pev[1]));
+        c->pacc.ms[kind] += ms;
+        c->pacc.launches[kind] += 1;
+    }
+    return HAWKES_OK;
+}
+
+int grid_for(hawkes_ctx* c, int64_t items, int per_sm = 8) {
+    int64_t g = (items + 255) / 256;
+    const int64_t cap = static_cast<int64_t>(c->sms) * per_sm;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : static_cast<int>(g);
+}
+
+void free_events(hawkes_ctx* c) {
+    dfree(c->t); dfree(c->x); dfree(c->y); dfree(c->s); dfree(c->scale_c); dfree(c->county);
+    dfree(c->lo); dfree(c->hi); dfree(c->tb); dfree(c->ev); dfree(c->acc); dfree(c->fixlist);
+    dfree(c->rows9);
+    c->rows9_cap = 0;
+    c->n = c->npad = c->nblk = 0;
+}
+
+void free_counties(hawkes_ctx* c) {
+    dfree(c->tri_county); dfree(c->tri_xy); dfree(c->tri_cum); dfree(c->cfirst); dfree(c->clast);
+    c->n_tri = 0;
+    c->counties_ok = false;
+}
+
+// Read and clear the latched device error (synchronous).
+int take_device_error(hawkes_ctx* c) {
+    int err = 0;
+    HK_CUDA(cudaMemcpyAsync(&err, c->ctr + CT_ERR, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    if (err != 0) HK_CUDA(cudaMemsetAsync(c->ctr + CT_ERR, 0, sizeof(int), c->stream));
+    return err;
+}
+
+bool params_ok(const hawkes_params* p) {
+    auto fin = [](double v) { return v == v && v - v == 0.0; };
+    return fin(p->mu) && fin(p->tau_x) && fin(p->tau_t) && fin(p->theta) && fin(p->omega) &&
+           fin(p->h) && p->mu >= 0 && p->theta >= 0 && p->tau_x > 0 && p->tau_t > 0 &&
+           p->omega > 0 && p->h > 0;
+}
+
+// Queue one log-likelihood evaluation over rows [rb, re).  d_params: device
+// parameters; d_out: 7 doubles; d_rows9: optional per-row output [9 n].
+int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags, int64_t rb,
+                   int64_t re, double* d_out, double* d_rows9) {
+    const bool f64 = (flags & HAWKES_F64) != 0;
+    const int model1 = (flags & HAWKES_MODEL1) ? 1 : 0;
+    const int prep_grid = grid_for(c, c->npad);
+    HK_TRY(timed(c, HAWKES_K_PREP, [&] {
+        k_prep<<<prep_grid, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->tb, d_params, model1,
+                                                  f64 ? 0 : 1, c->n, c->npad, c->ev, c->acc, c->cc,
+                                                  c->ctr, c->fix7);
+    }));
+    if (!f64) {
+        const bool sym = (rb == 0 && re == c->n);
+        HK_TRY(timed(c, HAWKES_K_SWEEP, [&] { launch_sweep(c, sym, rb, re); }));
+        HK_TRY(timed(c, HAWKES_K_FINAL, [&] {
+            k_finalize<<<c->final_blocks, 256, 0, c->stream>>>(c->acc, c->t, c->cc, c->npad, rb, re, 1,
+                                                               c->fixlist, c->ctr, c->partials,
+                                                               d_rows9);
+        }));
+        HK_TRY(timed(c, HAWKES_K_ROWS64, [&] {
+            k_rows64<<<c->sms, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc,
+                                                    model1, c->n, c->npad, 0, 0, 1, c->fixlist,
+                                                    c->ctr, c->acc, c->fix7, d_rows9);
+        }));
+    } else {
+        const int64_t count = re - rb;
+        int g = static_cast<int>(count < static_cast<int64_t>(c->sms) * 16 ? count : c->sms * 16);
+        if (g < 1) g = 1;
+        HK_TRY(timed(c, HAWKES_K_ROWS64, [&] {
+            k_rows64<<<g, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model1,
+                                               c->n, c->npad, rb, count, 0, c->fixlist, c->ctr,
+                                               c->acc, c->fix7, d_rows9);
+        }));
+        HK_TRY(timed(c, HAWKES_K_FINAL, [&] {
+            k_finalize<<<c->final_blocks, 256, 0, c->stream>>>(c->acc, c->t, c->cc, c->npad, rb, re, 0,
+                                                               c->fixlist, c->ctr, c->partials,
+                                                               d_rows9);
+        }));
+    }
+    HK_TRY(timed(c, HAWKES_K_REDUCE, [&] {
+        k_reduce<<<1, 256, 0, c->stream>>>(c->partials, c->final_blocks, c->fix7, c->cc, d_out,
+                                           c->ctr);
+    }));
+    return HAWKES_OK;
+}
+
+int sync_loglik(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int64_t rb, int64_t re,
+                double* out7, double* rows_host) {
+    if (!params_ok(p)) return HAWKES_ERR_ARG;
+    if ((flags & ~3u) != 0) return HAWKES_ERR_ARG;
+    HK_CUDA(cudaMemcpyAsync(c->params_dev, p, sizeof(hawkes_params), cudaMemcpyHostToDevice,
+                            c->stream));
+    double* d_rows9 = nullptr;
+    if (rows_host) {
+        if (c->rows9_cap < c->n) {
+            dfree(c->rows9);
+            HK_TRY(dalloc(&c->rows9, static_cast<size_t>(9 * c->n)));
+            c->rows9_cap = c->n;
+        }
+        d_rows9 = c->rows9;
+    }
+    HK_TRY(enqueue_loglik(c, c->params_dev, flags, rb, re, c->out_dev, d_rows9));
+    HK_CUDA(cudaMemcpyAsync(c->out_host, c->out_dev, 7 * sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+    if (rows_host)
+        HK_CUDA(cudaMemcpyAsync(rows_host, d_rows9, sizeof(double) * 9 * c->n,
+                                cudaMemcpyDeviceToHost, c->stream));
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    const int err = take_device_error(c);
+    if (err != 0) return err;
+    std::memcpy(out7, c->out_host, 7 * sizeof(double));
+    return HAWKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hawkes_strerror(int status) {
+    switch (status) {
+        case HAWKES_OK: return "ok";
+        case HAWKES_ERR_ARG: return "invalid argument";
+        case HAWKES_ERR_UNSORTED: return "event times not positive and non-decreasing";
+        case HAWKES_ERR_CUDA: return "CUDA runtime error";
+        case HAWKES_ERR_NONFINITE: return "non-finite result";
+        case HAWKES_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case HAWKES_ERR_OOM: return "device out of memory";
+        case HAWKES_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+int hawkes_create(hawkes_ctx** out, int device, void* cuda_stream) {
+    if (!out) return HAWKES_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return device < 0 ? HAWKES_ERR_ARG : HAWKES_ERR_CUDA;
+    }
+    DeviceGuard g(device);
+    hawkes_ctx* c = new (std::nothrow) hawkes_ctx();
+    if (!c) return HAWKES_ERR_OOM;
+    c->device = device;
+    int rc = HAWKES_OK;
+    do {
+        if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+            rc = HAWKES_ERR_CUDA;
+            break;
+        }
+        if (cuda_stream) {
+            c->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+                rc = HAWKES_ERR_CUDA;
+                break;
+            }
+            c->own_stream = true;
+        }
+        if (sweep_setup_attributes() != cudaSuccess) { rc = HAWKES_ERR_CUDA; break; }
+        c->sweep_grid = c->sms * sweep_blocks_per_sm();
+        c->final_blocks = 2 * c->sms;
+        if ((rc = dalloc(&c->ctr, CT_COUNT)) != HAWKES_OK) break;
+        if ((rc = dalloc(&c->cc, CC_COUNT)) != HAWKES_OK) break;
+        if ((rc = dalloc(&c->params_dev, 1)) != HAWKES_OK) break;
+        if ((rc = dalloc(&c->out_dev, 8)) != HAWKES_OK) break;
+        if ((rc = dalloc(&c->fix7, 8)) != HAWKES_OK) break;
+        if ((rc = dalloc(&c->partials, static_cast<size_t>(8 * c->final_blocks))) != HAWKES_OK) break;
+        if (cudaMallocHost(reinterpret_cast<void**>(&c->out_host), 8 * sizeof(double)) != cudaSuccess) {
+            rc = HAWKES_ERR_OOM;
+            break;
+        }
+        if (cudaEventCreate(&c->pev[0]) != cudaSuccess || cudaEventCreate(&c->pev[1]) != cudaSuccess) {
+            rc = HAWKES_ERR_CUDA;
+            break;
+        }
+        if (cudaMemsetAsync(c->ctr, 0, CT_COUNT * sizeof(int), c->stream) != cudaSuccess ||
+            cudaMemsetAsync(c->cc, 0, CC_COUNT * sizeof(double), c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            rc = HAWKES_ERR_CUDA;
+            break;
+        }
+    } while (0);
+    if (rc != HAWKES_OK) {
+        cudaGetLastError();
+        hawkes_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HAWKES_OK;
+}
+
+void hawkes_destroy(hawkes_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_events(c);
+    free_counties(c);
+    dfree(c->ctr); dfree(c->cc); dfree(c->params_dev); dfree(c->out_dev); dfree(c->fix7);
+    dfree(c->partials);
+    if (c->out_host) cudaFreeHost(c->out_host);
+    for (auto& e : c->pev)
+        if (e) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+int64_t hawkes_num_events(const hawkes_ctx* c) { return c ? c->n : 0; }
+
+int hawkes_set_events(hawkes_ctx* c, int64_t n, const double* t, const double* x, const double* y,
+                      const int32_t* county, int32_t n_counties, const double* county_scale) {
+    if (!c || n < 1 || !t || !county || n_counties < 1 || !county_scale) return HAWKES_ERR_ARG;
+    if ((x == nullptr) != (y == nullptr)) return HAWKES_ERR_ARG;
+    if (n > (int64_t(1) << 31) - 2 * TR) return HAWKES_ERR_ARG;  // 32-bit event indices
+    DeviceGuard g(c->device);
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    const int64_t npad = (n + TR - 1) / TR * TR;
+    int rc = HAWKES_OK;
+    auto fail = [&](int r) {
+        free_events(c);
+        return r;
+    };
+    if (!(c->t && c->n == n && c->n_counties == n_counties)) {
+        // new sizes: (re)allocate; county triangles survive if the county count does
+        const bool keep_counties = c->counties_ok && n_counties == c->n_counties;
+        free_events(c);
+        if (!keep_counties) free_counties(c);
+        c->n = n;
+        c->npad = npad;
+        c->nblk = npad / TB;
+        c->n_counties = n_counties;
+        if ((rc = dalloc(&c->t, npad)) || (rc = dalloc(&c->x, npad)) || (rc = dalloc(&c->y, npad)) ||
+            (rc = dalloc(&c->s, npad)) || (rc = dalloc(&c->scale_c, n_counties)) ||
+            (rc = dalloc(&c->county, n)) || (rc = dalloc(&c->lo, npad)) ||
+            (rc = dalloc(&c->hi, npad)) || (rc = dalloc(&c->tb, c->nblk)) ||
+            (rc = dalloc(&c->ev, npad)) || (rc = dalloc(&c->acc, 6 * npad)) ||
+            (rc = dalloc(&c->fixlist, npad)))
+            return fail(rc);
+    }
+    cudaStream_t st = c->stream;
+    if (cudaMemcpyAsync(c->t, t, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        (x && cudaMemcpyAsync(c->x, x, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+        (y && cudaMemcpyAsync(c->y, y, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+        cudaMemcpyAsync(c->county, county, n * sizeof(int32_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->scale_c, county_scale, n_counties * sizeof(double), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess)
+        return fail(HAWKES_ERR_CUDA);
+    rc = timed(c, HAWKES_K_OTHER, [&] {
+        k_setup<<<grid_for(c, npad), 256, 0, st>>>(c->t, c->x, c->y, c->county, n_counties,
+                                                   c->scale_c, n, npad, x ? 1 : 0, c->s, c->lo,
+                                                   c->hi, c->tb, c->ctr);
+    });
+    if (rc != HAWKES_OK) return fail(rc);
+    const int err = take_device_error(c);
+    if (err < 0) return fail(err);
+    return err;
+}
+
+int hawkes_set_counties(hawkes_ctx* c, int32_t n_tri, const int32_t* tri_county,
+                        const double* tri_xy) {
+    if (!c || n_tri < 1 || !tri_county || !tri_xy) return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    DeviceGuard g(c->device);
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    free_counties(c);
+    int rc;
+    if ((rc = dalloc(&c->tri_county, n_tri)) || (rc = dalloc(&c->tri_xy, 6 * (size_t)n_tri)) ||
+        (rc = dalloc(&c->tri_cum, n_tri)) || (rc = dalloc(&c->cfirst, c->n_counties)) ||
+        (rc = dalloc(&c->clast, c->n_counties))) {
+        free_counties(c);
+        return rc;
+    }
+    c->n_tri = n_tri;
+    cudaStream_t st = c->stream;
+    if (cudaMemcpyAsync(c->tri_county, tri_county, n_tri * sizeof(int32_t), cudaMemcpyHostToDevice,
+                        st) != cudaSuccess ||
+        cudaMemcpyAsync(c->tri_xy, tri_xy, 6 * (size_t)n_tri * sizeof(double),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        free_counties(c);
+        return HAWKES_ERR_CUDA;
+    }
+    rc = timed(c, HAWKES_K_OTHER, [&] {
+        k_tri_check<<<grid_for(c, n_tri), 256, 0, st>>>(c->tri_county, n_tri, c->n_counties, c->ctr);
+    });
+    if (rc == HAWKES_OK) rc = take_device_error(c);
+    if (rc == HAWKES_OK)
+        rc = timed(c, HAWKES_K_OTHER, [&] {
+            k_tri_area<<<grid_for(c, n_tri), 256, 0, st>>>(c->tri_xy, n_tri, c->tri_cum);
+        });
+    if (rc == HAWKES_OK)
+        rc = timed(c, HAWKES_K_OTHER, [&] {
+            k_tri_county<<<grid_for(c, c->n_counties), 256, 0, st>>>(
+                c->tri_county, n_tri, c->n_counties, c->tri_cum, c->cfirst, c->clast, c->ctr);
+        });
+    if (rc == HAWKES_OK) rc = take_device_error(c);
+    if (rc != HAWKES_OK) {
+        free_counties(c);
+        return rc;
+    }
+    c->counties_ok = true;
+    return HAWKES_OK;
+}
+
+int hawkes_resample_locations(hawkes_ctx* c, uint64_t seed, uint64_t stream, uint64_t iteration) {
+    if (!c) return HAWKES_ERR_ARG;
+    if (c->n == 0 || !c->counties_ok) return HAWKES_ERR_STATE;
+    DeviceGuard g(c->device);
+    return timed(c, HAWKES_K_RESAMPLE, [&] {
+        k_resample<<<grid_for(c, c->n), 256, 0, c->stream>>>(c->county, c->n, c->tri_xy, c->tri_cum,
+                                                             c->cfirst, c->clast, seed, stream,
+                                                             iteration, c->x, c->y);
+    });
+}
+
+int hawkes_get_locations(hawkes_ctx* c, double* x, double* y) {
+    if (!c || !x || !y) return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    DeviceGuard g(c->device);
+    HK_CUDA(cudaMemcpyAsync(x, c->x, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HK_CUDA(cudaMemcpyAsync(y, c->y, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    return HAWKES_OK;
+}
+
+int hawkes_loglik_grad(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int64_t row_begin,
+                       int64_t row_end, double* loglik, double* grad) {
+    if (!c || !p || !loglik || !grad) return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    if (row_begin < 0 || row_end > c->n || row_begin >= row_end) return HAWKES_ERR_ARG;
+    DeviceGuard g(c->device);
+    double out[7];
+    HK_TRY(sync_loglik(c, p, flags, row_begin, row_end, out, nullptr));
+    *loglik = out[0];
+    for (int k = 0; k < 6; ++k) grad[k] = out[1 + k];
+    return HAWKES_OK;
+}
+
+int hawkes_loglik_grad_async(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
+                             double* d_out) {
+    if (!c || !d_params || !d_out) return HAWKES_ERR_ARG;
+    if ((flags & ~3u) != 0) return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    DeviceGuard g(c->device);
+    return enqueue_loglik(c, d_params, flags, 0, c->n, d_out, nullptr);
+}
+
+int hawkes_loglik_rows(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, double* out7,
+                       double* rows) {
+    if (!c || !p || !out7 || !rows) return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    DeviceGuard g(c->device);
+    return sync_loglik(c, p, flags, 0, c->n, out7, rows);
+}
+
+int hawkes_profile_enable(hawkes_ctx* c, int on) {
+    if (!c) return HAWKES_ERR_ARG;
+    DeviceGuard g(c->device);
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    c->prof = on != 0;
+    if (c->prof) std::memset(&c->pacc, 0, sizeof(c->pacc));
+    return HAWKES_OK;
+}
+
+int hawkes_profile_read(hawkes_ctx* c, hawkes_profile* out) {
+    if (!c || !out) return HAWKES_ERR_ARG;
+    DeviceGuard g(c->device);
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    *out = c->pacc;
+    return HAWKES_OK;
+}
+
+}  // extern "C"

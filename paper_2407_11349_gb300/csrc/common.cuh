@@ -1,0 +1,197 @@
+// Shared definitions of the libhawkes CUDA sources: the context, the staged
+// event record, per-call constants and small PTX wrappers (mbarrier, bulk
+// TMA copy, SFU exp2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hawkes.h"
+
+namespace hk {
+
+// ---------------------------------------------------------------------------
+// Tiling of the N x N pair matrix.
+//   A warp owns WROWS = 32 * R rows (R per lane, strided by 32), a CTA owns
+//   TR = WARPS * WROWS rows.  Source (column) events are streamed through
+//   shared memory in tiles of TC events, one TMA bulk copy each.  Times are
+//   stored relative to the first event of their block of TB = TC events.
+// ---------------------------------------------------------------------------
+constexpr int R = 4;
+constexpr int WARPS = 8;
+constexpr int THREADS = WARPS * 32;
+constexpr int WROWS = 32 * R;
+constexpr int TR = WARPS * WROWS;
+constexpr int TC = 256;
+constexpr int TB = TC;
+static_assert(TC == THREADS, "column flush maps one thread to one column");
+static_assert(TB % WROWS == 0, "a warp's rows share one time block");
+static_assert(TR % TC == 0, "row tiles are whole column tiles");
+
+// Staged per-event record (32 B), rebuilt every call from the FP64 inputs
+// and the parameters.  Coordinates are pre-scaled so that a background
+// exponent is -(r~^2 + dt~^2) in base 2:
+//   x~ = x sqrt(a_x), a_x = log2(e) / (2 tau_x^2)   split hi + lo in FP32
+//   t~ = (t - T_block) sqrt(a_t), a_t = log2(e) / (2 tau_t^2)
+//   beta = tau_x^2 / (h^2 s^2)    (excitation spatial exponent is beta r~^2)
+//   ce = -2 log2(s)               (the 1 / s^2 of the source's density)
+struct __align__(16) Ev {
+    float t, xh, yh, beta;
+    float xl, yl, ce, pad;
+};
+static_assert(sizeof(Ev) == 32, "Ev is two 16-byte vectors");
+
+// Time value given to padding events: far after every real event, so that
+// every pair term with a padding event is exactly 0 (and finite products).
+constexpr float PAD_T = 1.0e15f;
+
+// Per-call constants, computed on the device from the parameters.
+enum {
+    CC_KX = 0,      // sqrt(a_x)
+    CC_KT,          // sqrt(a_t)
+    CC_OMT,         // omega log2(e) / sqrt(a_t): excitation time exponent per unit t~
+    CC_SR,          // 1 / a_x : r~^2 -> r^2
+    CC_ST,          // 1 / a_t : t~^2 -> t^2
+    CC_SET,         // 1 / sqrt(a_t) : t~ -> t
+    CC_SEQ,         // 2 h^2 / log2(e) : beta r~^2 -> r^2 / s^2
+    CC_CB,          // background normalisation 1 / ((2 pi)^{3/2} tau_x^2 tau_t)
+    CC_CE,          // excitation normalisation omega / (2 pi h^2)
+    CC_MU, CC_TX, CC_TT, CC_TH, CC_OM, CC_H,
+    CC_TN,          // t_N
+    CC_FLAGTHR,     // rows with lambda below this are recomputed in FP64
+    CC_VALID,       // 1 if the parameters are valid
+    CC_COUNT
+};
+
+// Device counters.
+enum {
+    CT_WORK = 0,    // persistent work-queue cursor
+    CT_FIX,         // number of rows queued for FP64 recomputation
+    CT_ERR,         // latched error status (0 or a HAWKES_ERR_* value)
+    CT_DONE,        // finished-block counter
+    CT_COUNT = 8
+};
+
+constexpr double LOG2E = 1.4426950408889634;
+constexpr double CLIP = 1e-40;
+constexpr double TWO_PI = 6.283185307179586;
+
+// Bounded spin: iterations of mbarrier.try_wait before a wait gives up.
+constexpr long long SPIN_LIMIT = 1ll << 22;
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One-dimensional bulk copy global -> shared through the TMA unit; completion
+// is signalled on `bar` as transferred bytes.  Addresses 16-byte aligned,
+// size a multiple of 16.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar` to complete; false if the bounded spin gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long long k = 0; k < SPIN_LIMIT; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// 2^x on the special-function unit; results below 2^-126 flush to zero.
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void set_error(int* ctr, int code) {
+    atomicCAS(ctr + CT_ERR, 0, code);
+}
+
+}  // namespace hk
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct hawkes_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 0;
+    int sweep_grid = 0;
+
+    int64_t n = 0, npad = 0;
+    int32_t n_counties = 0;
+    int64_t nblk = 0;
+
+    double* t = nullptr;       // [npad] FP64 times (padding = t_N)
+    double* x = nullptr;       // [npad] current locations
+    double* y = nullptr;
+    double* s = nullptr;       // [npad] per-event source scale
+    double* scale_c = nullptr; // [n_counties]
+    int32_t* county = nullptr; // [n]
+    int32_t* lo = nullptr;     // [npad] first index with t_j == t_i
+    int32_t* hi = nullptr;     // [npad] one past the last index with t_j == t_i
+    double* tb = nullptr;      // [npad / TB] block time bases
+    hk::Ev* ev = nullptr;      // [npad] staged FP32 records
+    double* acc = nullptr;     // [6 * npad] per-row moment sums (natural units)
+    double* partials = nullptr;// [final_blocks * 8]
+    double* fix7 = nullptr;    // [8] sums over FP64-recomputed rows
+    int* fixlist = nullptr;    // [npad]
+    int* ctr = nullptr;        // [CT_COUNT]
+    double* cc = nullptr;      // [CC_COUNT]
+    hawkes_params* params_dev = nullptr;
+    double* out_dev = nullptr; // [8]
+    double* out_host = nullptr;// pinned [8]
+    double* rows9 = nullptr;   // [9 * n] optional per-row output (allocated on demand)
+    int64_t rows9_cap = 0;
+    int final_blocks = 0;
+
+    int32_t n_tri = 0;
+    bool counties_ok = false;
+    int32_t* tri_county = nullptr;
+    double* tri_xy = nullptr;
+    double* tri_cum = nullptr;
+    int32_t* cfirst = nullptr;
+    int32_t* clast = nullptr;
+
+    bool prof = false;
+    cudaEvent_t pev[2] = {nullptr, nullptr};
+    hawkes_profile pacc{};
+};

@@ -1,0 +1,238 @@
+"""Python binding of libhawkes (include/hawkes.h): argument marshalling only.
+
+Every computation runs in the CUDA library; there is no CPU fallback.  If the
+shared library is missing, importing the binding raises: build it first with
+``python -c "import __graft_entry__ as g; g.build()"`` (or
+``paper_2407_11349_gb300.build.build()``).
+
+The module-level functions carry the C names (``hawkes_create``,
+``hawkes_loglik_grad``, ...) and take the same arguments as host arrays or
+device pointers; the ``Hawkes`` class wraps one context for convenience.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libhawkes.so")
+
+HAWKES_OK = 0
+HAWKES_F32 = 0
+HAWKES_F64 = 1
+HAWKES_MODEL2 = 0
+HAWKES_MODEL1 = 2
+KERNEL_CLASSES = ("prep", "sweep", "rows64", "final", "reduce", "resample", "other")
+
+
+class HawkesError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+class hawkes_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("mu", "tau_x", "tau_t", "theta", "omega", "h")]
+
+
+class hawkes_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_VP = ctypes.c_void_p
+_lib = None
+
+# name -> (restype, argtypes), mirroring include/hawkes.h
+_SIGS = {
+    "hawkes_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "hawkes_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _VP]),
+    "hawkes_destroy": (None, [_VP]),
+    "hawkes_set_events": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D, _D, _I32, ctypes.c_int32, _D]),
+    "hawkes_set_counties": (ctypes.c_int, [_VP, ctypes.c_int32, _I32, _D]),
+    "hawkes_resample_locations": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]),
+    "hawkes_get_locations": (ctypes.c_int, [_VP, _D, _D]),
+    "hawkes_loglik_grad": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_params), ctypes.c_uint32,
+                                          ctypes.c_int64, ctypes.c_int64, _D, _D]),
+    "hawkes_loglik_grad_async": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, _VP]),
+    "hawkes_loglik_rows": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_params), ctypes.c_uint32, _D, _D]),
+    "hawkes_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "hawkes_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_profile)]),
+    "hawkes_num_events": (ctypes.c_int64, [_VP]),
+}
+
+
+def lib():
+    """The loaded libhawkes (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libhawkes.so not built ({LIB_PATH}); run the package build first")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(status):
+    return lib().hawkes_strerror(int(status)).decode()
+
+
+def _check(rc, where):
+    if rc != HAWKES_OK:
+        raise HawkesError(rc, where)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def as_params(p):
+    if isinstance(p, hawkes_params):
+        return p
+    p = [float(v) for v in p]
+    return hawkes_params(*p)
+
+
+# --- C-named thin wrappers -------------------------------------------------
+
+def hawkes_create(device=0, stream=0):
+    h = _VP()
+    _check(lib().hawkes_create(ctypes.byref(h), int(device), _VP(int(stream) or None)), "hawkes_create")
+    return h
+
+
+def hawkes_destroy(ctx):
+    lib().hawkes_destroy(ctx)
+
+
+def hawkes_set_events(ctx, t, x, y, county, county_scale):
+    t, x, y, cs = _f64(t), _f64(x), _f64(y), _f64(county_scale)
+    county = np.ascontiguousarray(county, dtype=np.int32)
+    _check(lib().hawkes_set_events(ctx, t.shape[0], _dp(t), _dp(x), _dp(y), county.ctypes.data_as(_I32),
+                                   cs.shape[0], _dp(cs)), "hawkes_set_events")
+
+
+def hawkes_set_counties(ctx, tri_county, tri_xy):
+    tc = np.ascontiguousarray(tri_county, dtype=np.int32)
+    txy = np.ascontiguousarray(tri_xy, dtype=np.float64).reshape(-1)
+    _check(lib().hawkes_set_counties(ctx, tc.shape[0], tc.ctypes.data_as(_I32), _dp(txy)),
+           "hawkes_set_counties")
+
+
+def hawkes_resample_locations(ctx, seed, stream, iteration):
+    _check(lib().hawkes_resample_locations(ctx, int(seed), int(stream), int(iteration)),
+           "hawkes_resample_locations")
+
+
+def hawkes_get_locations(ctx):
+    n = lib().hawkes_num_events(ctx)
+    x, y = np.empty(n), np.empty(n)
+    _check(lib().hawkes_get_locations(ctx, _dp(x), _dp(y)), "hawkes_get_locations")
+    return x, y
+
+
+def hawkes_loglik_grad(ctx, params, flags=HAWKES_F32, row_begin=0, row_end=None):
+    n = lib().hawkes_num_events(ctx)
+    row_end = n if row_end is None else row_end
+    ll = ctypes.c_double()
+    g = np.zeros(6)
+    p = as_params(params)
+    _check(lib().hawkes_loglik_grad(ctx, ctypes.byref(p), int(flags), int(row_begin), int(row_end),
+                                    ctypes.byref(ll), _dp(g)), "hawkes_loglik_grad")
+    return ll.value, g
+
+
+def hawkes_loglik_grad_async(ctx, d_params, flags, d_out):
+    """d_params, d_out: device addresses (e.g. torch ``tensor.data_ptr()``)."""
+    _check(lib().hawkes_loglik_grad_async(ctx, _VP(int(d_params)), int(flags), _VP(int(d_out))),
+           "hawkes_loglik_grad_async")
+
+
+def hawkes_loglik_rows(ctx, params, flags=HAWKES_F32):
+    n = lib().hawkes_num_events(ctx)
+    out = np.zeros(7)
+    rows = np.zeros((n, 9))
+    p = as_params(params)
+    _check(lib().hawkes_loglik_rows(ctx, ctypes.byref(p), int(flags), _dp(out), _dp(rows)),
+           "hawkes_loglik_rows")
+    return out, rows
+
+
+def hawkes_profile_enable(ctx, on):
+    _check(lib().hawkes_profile_enable(ctx, 1 if on else 0), "hawkes_profile_enable")
+
+
+def hawkes_profile_read(ctx):
+    pr = hawkes_profile()
+    _check(lib().hawkes_profile_read(ctx, ctypes.byref(pr)), "hawkes_profile_read")
+    return {k: (int(pr.launches[i]), float(pr.ms[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def hawkes_num_events(ctx):
+    return int(lib().hawkes_num_events(ctx))
+
+
+# --- convenience wrapper ---------------------------------------------------
+
+class Hawkes:
+    """One libhawkes context on one GPU."""
+
+    def __init__(self, device=0, stream=0):
+        self.ctx = hawkes_create(device, stream)
+
+    def close(self):
+        if self.ctx:
+            hawkes_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_events(self, t, county, county_scale, x=None, y=None):
+        hawkes_set_events(self.ctx, t, x, y, county, county_scale)
+
+    def set_counties(self, tri_county, tri_xy):
+        hawkes_set_counties(self.ctx, tri_county, tri_xy)
+
+    def load(self, ds, counties=True):
+        """Events and county triangles of a ``synth.Dataset``."""
+        self.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+        if counties:
+            self.set_counties(ds.counties.tri_county, ds.counties.tri_xy)
+        return self
+
+    def resample(self, seed, stream, iteration):
+        hawkes_resample_locations(self.ctx, seed, stream, iteration)
+
+    def locations(self):
+        return hawkes_get_locations(self.ctx)
+
+    def loglik_grad(self, params, flags=HAWKES_F32, row_begin=0, row_end=None):
+        return hawkes_loglik_grad(self.ctx, params, flags, row_begin, row_end)
+
+    def loglik_grad_async(self, d_params, d_out, flags=HAWKES_F32):
+        hawkes_loglik_grad_async(self.ctx, d_params, flags, d_out)
+
+    def loglik_rows(self, params, flags=HAWKES_F32):
+        return hawkes_loglik_rows(self.ctx, params, flags)
+
+    def profile(self, on=None):
+        if on is not None:
+            hawkes_profile_enable(self.ctx, on)
+        return hawkes_profile_read(self.ctx)
+
+    @property
+    def n(self):
+        return hawkes_num_events(self.ctx)

@@ -1,0 +1,214 @@
+"""libhawkes (CUDA, called through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (stated once, used everywhere below):
+  FP64 GPU path: every output within 1e-10 relative of the oracle.
+  FP32 GPU path: the log-likelihood within 1e-6 relative; each gradient
+    component within 1e-5 relative, measured against max(|g_k|, 1e-3 S_k)
+    where S_k = sum_i |d ell_i / d p_k| (the scale of the component's terms,
+    so that a component that happens to cancel to near zero is judged on the
+    size of what cancelled).
+  Per-row values (FP32): log lambda_i within 2e-6 absolute (a relative rate
+    error); Lambda_i within 1e-12 relative (computed in FP64 on both sides).
+  Resample: bit-identical coordinates.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2407_11349_gb300 import synth
+from paper_2407_11349_gb300.hawkes import (HAWKES_F32, HAWKES_F64, HAWKES_MODEL1, Hawkes,
+                                           HawkesError)
+
+pytestmark = pytest.mark.gpu
+
+P0 = synth.DEFAULT_PARAMS
+TOL_F64 = 1e-10
+TOL_LL32 = 1e-6
+TOL_G32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def hk():
+    h = Hawkes(0)
+    yield h
+    h.close()
+
+
+def small_grid(n, seed=0, T=100.0):
+    return synth.grid_dataset(n, T, 20, 20, seed=seed)
+
+
+def oracle_rows(ds, p=P0, model1=False):
+    s = None if model1 else ds.s
+    return oracle.loglik_grad(ds.t, ds.x, ds.y, p, s=s, rows=True)
+
+
+def assert_close(got_ll, got_g, ref, ref_rows, tol_ll, tol_g, what=""):
+    scale = np.abs(ref_rows[:, 1:7]).sum(axis=0)
+    e_ll = abs(got_ll - ref[0]) / max(abs(ref[0]), 1e-300)
+    denom = np.maximum(np.abs(ref[1:]), 1e-3 * scale)
+    denom = np.where(denom > 0, denom, 1.0)
+    e_g = np.abs(got_g - ref[1:]) / denom
+    assert e_ll <= tol_ll, f"{what} loglik rel err {e_ll:.3g} > {tol_ll}"
+    assert np.all(e_g <= tol_g), f"{what} grad rel errs {e_g} > {tol_g}"
+    return e_ll, e_g
+
+
+def check_both(hk, ds, p=P0, model1=False, what=""):
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle_rows(ds, p, model1)
+    fl = HAWKES_MODEL1 if model1 else 0
+    ll64, g64 = hk.loglik_grad(p, HAWKES_F64 | fl)
+    assert_close(ll64, g64, ref, rows, TOL_F64, TOL_F64, what + " f64")
+    ll32, g32 = hk.loglik_grad(p, HAWKES_F32 | fl)
+    return assert_close(ll32, g32, ref, rows, TOL_LL32, TOL_G32, what + " f32")
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 255, 256, 257, 1023, 1024, 1025, 2049, 5000])
+def test_sizes_and_ragged_tails(hk, n):
+    check_both(hk, small_grid(n, seed=n), what=f"n={n}")
+
+
+def test_workload_c1(hk):
+    """N=2,000, 20x20 grid, seed 0: the small configuration, both paths."""
+    ds = synth.config_dataset("c1")
+    check_both(hk, ds, what="c1")
+    out, rows = hk.loglik_rows(P0, HAWKES_F32)
+    ref, rrows = oracle_rows(ds)
+    assert np.max(np.abs(rows[:, 7] - rrows[:, 7])) < 2e-6
+    assert np.max(np.abs(rows[:, 8] - rrows[:, 8]) / np.abs(rrows[:, 8])) < 1e-12
+
+
+def test_ties_integer_days(hk):
+    ds = synth.integer_day_times(small_grid(3000, seed=5))
+    assert np.sum(np.diff(ds.t) == 0) > 2500
+    check_both(hk, ds, what="ties")
+
+
+def test_model1_flag(hk):
+    check_both(hk, small_grid(1500, seed=6), model1=True, what="model1")
+
+
+@pytest.mark.parametrize("p", [(0.5, 20.0, 7.0, 0.0, 0.2, 2.0), (0.0, 20.0, 7.0, 0.3, 0.2, 2.0),
+                               (2.0, 5.0, 2.0, 0.9, 1.5, 0.7)])
+def test_degenerate_and_other_parameters(hk, p):
+    check_both(hk, small_grid(1800, seed=7), p=p, what=f"p={p}")
+
+
+def test_row_windows_sum_to_whole(hk):
+    ds = small_grid(4100, seed=8)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle_rows(ds)
+    cuts = [0, 700, 2500, 3072, ds.n]
+    for flags, tl, tg in ((HAWKES_F64, TOL_F64, TOL_F64), (HAWKES_F32, TOL_LL32, TOL_G32)):
+        tot_ll, tot_g = 0.0, np.zeros(6)
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            ll, g = hk.loglik_grad(P0, flags, a, b)
+            wref = oracle.loglik_grad(ds.t, ds.x, ds.y, P0, s=ds.s, row_begin=a, row_end=b)
+            assert_close(ll, g, wref, rows[a:b], tl, tg, f"window [{a},{b})")
+            tot_ll += ll
+            tot_g += g
+        assert_close(tot_ll, tot_g, ref, rows, tl, tg, "sum of windows")
+
+
+def test_async_matches_sync(hk):
+    torch = pytest.importorskip("torch")
+    ds = small_grid(3000, seed=9)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ll, g = hk.loglik_grad(P0, HAWKES_F32)
+    dp = torch.tensor(P0, dtype=torch.float64, device="cuda")
+    dout = torch.zeros(7, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    hk.loglik_grad_async(dp.data_ptr(), dout.data_ptr(), HAWKES_F32)
+    hk.profile()  # waits for the context stream
+    o = dout.cpu().numpy()
+    assert abs(o[0] - ll) <= 1e-12 * abs(ll)
+    assert np.allclose(o[1:], g, rtol=1e-12, atol=0)
+
+
+def test_resample_bit_exact(hk):
+    for ds in (synth.config_dataset("c1"),
+               synth.voronoi_dataset(20_000, n_cells=300, seed=10)):
+        hk.load(ds)
+        for it in (0, 1, 17):
+            hk.resample(1234, 5, it)
+            gx, gy = hk.locations()
+            ox, oy = oracle.resample(ds.county, ds.counties.n, ds.counties.tri_county,
+                                     ds.counties.tri_xy, 1234, 5, it)
+            assert np.array_equal(gx, ox) and np.array_equal(gy, oy), f"iteration {it}"
+        # the likelihood then uses the resampled locations
+        ll, g = hk.loglik_grad(P0, HAWKES_F32)
+        if ds.n <= 2000:
+            ref, rows = oracle.loglik_grad(ds.t, ox, oy, P0, s=ds.s, rows=True)
+            assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, "after resample")
+
+
+def test_invalid_input_is_reported(hk):
+    ds = small_grid(100, seed=11)
+    with pytest.raises(HawkesError) as e:
+        hk.set_events(ds.t[::-1].copy(), ds.county, ds.county_scale, ds.x, ds.y)
+    assert e.value.status == -2
+    with pytest.raises(HawkesError) as e:
+        bad = ds.county.copy()
+        bad[3] = 10_000
+        hk.set_events(ds.t, bad, ds.county_scale, ds.x, ds.y)
+    assert e.value.status == -1
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    with pytest.raises(HawkesError):
+        hk.loglik_grad((0.5, -1.0, 7.0, 0.3, 0.2, 2.0))
+    with pytest.raises(HawkesError):
+        hk.loglik_grad(P0, HAWKES_F32, 50, 10)
+    ll, g = hk.loglik_grad(P0)  # the context stays usable
+    assert np.isfinite(ll)
+
+
+def test_c2_sampled_rows_and_paths(hk):
+    """N=100,000 (60x60 grid, 1,200 d) after one resample: FP32 rows against the
+    oracle one by one on sampled rows; FP32 totals against the FP64 GPU path."""
+    ds = synth.config_dataset("c2")
+    hk.load(ds)
+    hk.resample(1, 0, 0)
+    x, y = hk.locations()
+    out32, rows32 = hk.loglik_rows(P0, HAWKES_F32)
+    ll64, g64 = hk.loglik_grad(P0, HAWKES_F64)
+    rng = np.random.default_rng(0)
+    idx = np.concatenate([[0, 1, ds.n - 1], rng.choice(ds.n, 61, replace=False)])
+    ref = np.stack([oracle.loglik_grad(ds.t, x, y, P0, s=ds.s, row_begin=i, row_end=i + 1,
+                                       rows=True)[1][0] for i in idx])
+    got = rows32[idx]
+    assert np.max(np.abs(got[:, 7] - ref[:, 7])) < 2e-6
+    assert np.max(np.abs(got[:, 8] - ref[:, 8]) / np.abs(ref[:, 8])) < 1e-12
+    gscale = np.abs(ref[:, 1:7]).max(axis=0)
+    assert np.all(np.abs(got[:, 1:7] - ref[:, 1:7]) <= TOL_G32 * np.maximum(np.abs(ref[:, 1:7]), 1e-3 * gscale))
+    # totals: FP32 against the FP64 GPU path (itself pinned to the oracle above)
+    ref7 = np.concatenate([[ll64], g64])
+    assert_close(out32[0], out32[1:], ref7, rows32, TOL_LL32, TOL_G32, "c2 f32 vs f64")
+
+
+def test_c3_full_size_sampled(hk):
+    """N=1,000,000 Voronoi workload in the benchmark's launch configuration:
+    sampled rows against the oracle, and row shards summing to the whole."""
+    ds = synth.config_dataset("c3")
+    hk.load(ds)
+    hk.resample(2, 0, 0)
+    x, y = hk.locations()
+    out32, rows32 = hk.loglik_rows(P0, HAWKES_F32)
+    assert np.all(np.isfinite(out32))
+    rng = np.random.default_rng(1)
+    idx = np.concatenate([[0, ds.n // 2, ds.n - 1], rng.choice(ds.n, 21, replace=False)])
+    ref = np.stack([oracle.loglik_grad(ds.t, x, y, P0, s=ds.s, row_begin=i, row_end=i + 1,
+                                       rows=True)[1][0] for i in idx])
+    got = rows32[idx]
+    assert np.max(np.abs(got[:, 7] - ref[:, 7])) < 2e-6
+    assert np.max(np.abs(got[:, 8] - ref[:, 8]) / np.abs(ref[:, 8])) < 1e-12
+    gscale = np.abs(ref[:, 1:7]).max(axis=0)
+    assert np.all(np.abs(got[:, 1:7] - ref[:, 1:7]) <= TOL_G32 * np.maximum(np.abs(ref[:, 1:7]), 1e-3 * gscale))
+    # the sum over rows of the per-row values is the total
+    assert abs(rows32[:, 0].sum() - out32[0]) <= 1e-9 * abs(out32[0])
+    # shards (window kernel, no symmetric shortcut) sum to the symmetric whole
+    cuts = [0, 400_000, 700_000, ds.n]
+    tot = np.zeros(7)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        ll, g = hk.loglik_grad(P0, HAWKES_F32, a, b)
+        tot += np.concatenate([[ll], g])
+    assert_close(tot[0], tot[1:], out32, rows32, TOL_LL32, TOL_G32, "c3 shards")
