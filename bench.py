@@ -131,14 +131,15 @@ def cpu_baseline(ds, seconds=15.0):
     x, y, s = ds.x, ds.y, ds.s
     p = ds.params
     mid = n // 2
-    m = max(threads, 16)
-    t0 = time.perf_counter()
-    oracle.loglik_grad(ds.t, x, y, p, s=s, row_begin=mid, row_end=mid + m, threads=threads)
-    dt = time.perf_counter() - t0
-    m = int(min(n - mid, max(m, m * seconds / max(dt, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.loglik_grad(ds.t, x, y, p, s=s, row_begin=mid, row_end=mid + m, threads=threads)
-    dt = time.perf_counter() - t0
+    m = 4 * threads
+    while True:  # grow the window until it takes about `seconds`
+        m = min(m, n - mid)
+        t0 = time.perf_counter()
+        oracle.loglik_grad(ds.t, x, y, p, s=s, row_begin=mid, row_end=mid + m, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.6 * seconds or m >= n - mid:
+            break
+        m = int(m * min(8.0, 1.1 * seconds / max(dt, 1e-3)))
     # m rows x (n - 1) sources = m (n - 1) / 2 unordered-pair equivalents of the full sum
     value = m * (n - 1) / 2 / dt
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -157,12 +158,17 @@ def run_reference(args):
     threads = oracle.max_threads()
     n, mid = ds.n, ds.n // 2
     # size each step so the whole run stays within a few minutes
-    m = max(threads, 16)
-    t0 = time.perf_counter()
-    oracle.loglik_grad(ds.t, ds.x, ds.y, ds.params, s=ds.s, row_begin=mid, row_end=mid + m, threads=threads)
-    per_row = (time.perf_counter() - t0) / m
     budget = 150.0 / max(args.steps + args.warmup, 1)
-    m = int(max(threads, min(n - mid, budget / per_row)))
+    m = 4 * threads
+    while True:
+        m = min(m, n - mid)
+        t0 = time.perf_counter()
+        oracle.loglik_grad(ds.t, ds.x, ds.y, ds.params, s=ds.s, row_begin=mid, row_end=mid + m,
+                           threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.6 * budget or m >= n - mid:
+            break
+        m = int(m * min(8.0, 1.1 * budget / max(dt, 1e-3)))
     times = []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -193,6 +199,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="sweep kernel variant (default: autotuned)")
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"],
+                    help="c3 (default) is the benchmark; c1/c2 are smaller cases for profiling")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -210,7 +220,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    ds = synth.config_dataset("c3")
+    ds = synth.config_dataset(args.workload)
     n = ds.n
     pairs = n * (n - 1) / 2
     stream = torch.cuda.current_stream()
@@ -218,6 +228,12 @@ def main():
     hk.load(ds)
     p = ds.params
     chain = rank  # each rank is an independent chain replica
+    hk.resample(2, chain, 0)
+    if args.variant >= 0:
+        hk.set_variant(args.variant)
+        variant, tune_ms = args.variant, []
+    else:
+        variant, tune_ms = hk.tune(p, reps=1)  # autotuner: fastest sweep variant for this N
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
@@ -289,7 +305,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000 * T / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_events": n, "pairs_per_step": pairs,
+            "config": {"workload": WORKLOAD if args.workload == "c3" else args.workload, "n_events": n, "pairs_per_step": pairs,
                        "chains": world, "l2": "256 MB buffer written between timed steps",
                        "loglik": ll, "grad": list(map(float, g))},
             "gpu_launches": int(launches),
@@ -297,7 +313,8 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                          "unit": "Top/s", "frac": achieved_ops / peak_ops,
                          "traffic": profiled_traffic(),
-                         "kernel": "k_sweep<true> (FP32 pair sweep)",
+                         "kernel": f"k_sweep variant {variant} (FP32 pair sweep)",
+                         "tuned_ms": [round(float(x), 3) for x in tune_ms],
                          "per_unit": f"{ALG_FP32_OPS_PER_PAIR} FP32 lane ops per unordered pair",
                          "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
                                         f"(sm_max_mhz, {pk_src})",

@@ -179,6 +179,26 @@ int hawkes_profile_enable(hawkes_ctx* ctx, int on);
 /* Wait for queued work and read the counters. */
 int hawkes_profile_read(hawkes_ctx* ctx, hawkes_profile* out);
 
+/*
+ * Kernel variants of the FP32 pair sweep (rows per thread, resident CTAs per
+ * SM).  All give the same result up to FP32 summation order; they differ in
+ * speed by problem size.  hawkes_sweep_variants() is their number;
+ * hawkes_set_sweep_variant selects one (synchronous; rebuilds the work list).
+ */
+int hawkes_sweep_variants(void);
+int hawkes_set_sweep_variant(hawkes_ctx* ctx, int variant);
+int hawkes_get_sweep_variant(const hawkes_ctx* ctx);
+
+/*
+ * Autotune the sweep on the current events: run every variant `reps` times
+ * (after one warm-up) at `params` (host pointer; flags as for
+ * hawkes_loglik_grad, FP32 path), time the sweep kernel with CUDA events,
+ * keep the fastest.  *chosen receives its index; ms (optional, length
+ * hawkes_sweep_variants()) the mean sweep time of each variant.
+ */
+int hawkes_tune(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags, int reps,
+                int* chosen, double* ms);
+
 /* Number of events n of the current set (0 if none). */
 int64_t hawkes_num_events(const hawkes_ctx* ctx);
 

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -11,7 +12,7 @@ namespace hk {
 __global__ void k_setup(double*, double*, double*, const int32_t*, int32_t, const double*, int64_t,
                         int64_t, int, double*, int32_t*, int32_t*, double*, int*);
 __global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
-                       const hawkes_params*, int, int, int64_t, int64_t, Ev*, double*, double*,
+                       const hawkes_params*, int, int, int64_t, int64_t, Rec*, double*, double*,
                        int*, double*);
 __global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
                            int, int*, int*, double*, double*);
@@ -26,7 +27,9 @@ __global__ void k_resample(const int32_t*, int64_t, const double*, const double*
                            const int32_t*, uint64_t, uint64_t, uint64_t, double*, double*);
 // sweep.cu
 cudaError_t sweep_setup_attributes();
-int sweep_blocks_per_sm();
+int sweep_num_variants();
+int sweep_blocks_per_sm(int v);
+std::vector<int4> sweep_items(int64_t n, int v);
 cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end);
 }  // namespace hk
 
@@ -102,7 +105,10 @@ int grid_for(hawkes_ctx* c, int64_t items, int per_sm = 8) {
 
 void free_events(hawkes_ctx* c) {
     dfree(c->t); dfree(c->x); dfree(c->y); dfree(c->s); dfree(c->scale_c); dfree(c->county);
-    dfree(c->lo); dfree(c->hi); dfree(c->tb); dfree(c->ev); dfree(c->acc); dfree(c->fixlist);
+    dfree(c->lo); dfree(c->hi); dfree(c->tb); dfree(c->rec); dfree(c->acc); dfree(c->fixlist);
+    dfree(c->items);
+    c->nitems = 0;
+    c->items_variant = -1;
     dfree(c->rows9);
     c->rows9_cap = 0;
     c->n = c->npad = c->nblk = 0;
@@ -130,6 +136,28 @@ bool params_ok(const hawkes_params* p) {
            p->omega > 0 && p->h > 0;
 }
 
+// (Re)build the symmetric work list for the current events and kernel
+// variant (synchronous; never called while a stream is being captured).
+int ensure_items(hawkes_ctx* c) {
+    if (c->items && c->items_variant == c->variant) return HAWKES_OK;
+    dfree(c->items);
+    const std::vector<int4> items = sweep_items(c->n, c->variant);
+    HK_TRY(dalloc(&c->items, items.size()));
+    HK_CUDA(cudaMemcpyAsync(c->items, items.data(), items.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, c->stream));
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    c->nitems = static_cast<int>(items.size());
+    c->items_variant = c->variant;
+    return HAWKES_OK;
+}
+
+int select_variant(hawkes_ctx* c, int v) {
+    if (v < 0 || v >= sweep_num_variants()) return HAWKES_ERR_ARG;
+    c->variant = v;
+    c->variant_bpsm = sweep_blocks_per_sm(v);
+    return c->n ? ensure_items(c) : HAWKES_OK;
+}
+
 // Queue one log-likelihood evaluation over rows [rb, re).  d_params: device
 // parameters; d_out: 7 doubles; d_rows9: optional per-row output [9 n].
 int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags, int64_t rb,
@@ -139,7 +167,7 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
     const int prep_grid = grid_for(c, c->npad);
     HK_TRY(timed(c, HAWKES_K_PREP, [&] {
         k_prep<<<prep_grid, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->tb, d_params, model1,
-                                                  f64 ? 0 : 1, c->n, c->npad, c->ev, c->acc, c->cc,
+                                                  f64 ? 0 : 1, c->n, c->npad, c->rec, c->acc, c->cc,
                                                   c->ctr, c->fix7);
     }));
     if (!f64) {
@@ -251,7 +279,8 @@ int hawkes_create(hawkes_ctx** out, int device, void* cuda_stream) {
             c->own_stream = true;
         }
         if (sweep_setup_attributes() != cudaSuccess) { rc = HAWKES_ERR_CUDA; break; }
-        c->sweep_grid = c->sms * sweep_blocks_per_sm();
+        c->variant = 0;
+        c->variant_bpsm = sweep_blocks_per_sm(0);
         c->final_blocks = 2 * c->sms;
         if ((rc = dalloc(&c->ctr, CT_COUNT)) != HAWKES_OK) break;
         if ((rc = dalloc(&c->cc, CC_COUNT)) != HAWKES_OK) break;
@@ -305,10 +334,10 @@ int hawkes_set_events(hawkes_ctx* c, int64_t n, const double* t, const double* x
                       const int32_t* county, int32_t n_counties, const double* county_scale) {
     if (!c || n < 1 || !t || !county || n_counties < 1 || !county_scale) return HAWKES_ERR_ARG;
     if ((x == nullptr) != (y == nullptr)) return HAWKES_ERR_ARG;
-    if (n > (int64_t(1) << 31) - 2 * TR) return HAWKES_ERR_ARG;  // 32-bit event indices
+    if (n > (int64_t(1) << 31) - 2 * NPAD_MULT) return HAWKES_ERR_ARG;  // 32-bit event indices
     DeviceGuard g(c->device);
     HK_CUDA(cudaStreamSynchronize(c->stream));
-    const int64_t npad = (n + TR - 1) / TR * TR;
+    const int64_t npad = (n + NPAD_MULT - 1) / NPAD_MULT * NPAD_MULT;
     int rc = HAWKES_OK;
     auto fail = [&](int r) {
         free_events(c);
@@ -327,7 +356,7 @@ int hawkes_set_events(hawkes_ctx* c, int64_t n, const double* t, const double* x
             (rc = dalloc(&c->s, npad)) || (rc = dalloc(&c->scale_c, n_counties)) ||
             (rc = dalloc(&c->county, n)) || (rc = dalloc(&c->lo, npad)) ||
             (rc = dalloc(&c->hi, npad)) || (rc = dalloc(&c->tb, c->nblk)) ||
-            (rc = dalloc(&c->ev, npad)) || (rc = dalloc(&c->acc, 6 * npad)) ||
+            (rc = dalloc(&c->rec, npad)) || (rc = dalloc(&c->acc, 6 * npad)) ||
             (rc = dalloc(&c->fixlist, npad)))
             return fail(rc);
     }
@@ -347,7 +376,10 @@ int hawkes_set_events(hawkes_ctx* c, int64_t n, const double* t, const double* x
     if (rc != HAWKES_OK) return fail(rc);
     const int err = take_device_error(c);
     if (err < 0) return fail(err);
-    return err;
+    c->items_variant = -1;
+    rc = ensure_items(c);
+    if (rc != HAWKES_OK) return fail(rc);
+    return HAWKES_OK;
 }
 
 int hawkes_set_counties(hawkes_ctx* c, int32_t n_tri, const int32_t* tri_county,
@@ -444,6 +476,48 @@ int hawkes_loglik_rows(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, do
     if (c->n == 0) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
     return sync_loglik(c, p, flags, 0, c->n, out7, rows);
+}
+
+int hawkes_sweep_variants(void) { return sweep_num_variants(); }
+
+int hawkes_set_sweep_variant(hawkes_ctx* c, int variant) {
+    if (!c) return HAWKES_ERR_ARG;
+    DeviceGuard g(c->device);
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    return select_variant(c, variant);
+}
+
+int hawkes_get_sweep_variant(const hawkes_ctx* c) { return c ? c->variant : HAWKES_ERR_ARG; }
+
+int hawkes_tune(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int reps, int* chosen,
+                double* ms) {
+    if (!c || !p || reps < 1) return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    if (!params_ok(p) || (flags & ~(uint32_t)HAWKES_MODEL1) != 0) return HAWKES_ERR_ARG;
+    DeviceGuard g(c->device);
+    const bool prof = c->prof;
+    const hawkes_profile saved = c->pacc;
+    int best = -1;
+    double best_ms = 0.0;
+    double out7[7];
+    for (int v = 0; v < sweep_num_variants(); ++v) {
+        HK_TRY(select_variant(c, v));
+        HK_TRY(sync_loglik(c, p, flags, 0, c->n, out7, nullptr));  // warm-up
+        c->prof = true;
+        std::memset(&c->pacc, 0, sizeof(c->pacc));
+        for (int r = 0; r < reps; ++r) HK_TRY(sync_loglik(c, p, flags, 0, c->n, out7, nullptr));
+        const double t = c->pacc.ms[HAWKES_K_SWEEP] / reps;
+        c->prof = prof;
+        if (ms) ms[v] = t;
+        if (best < 0 || t < best_ms) {
+            best = v;
+            best_ms = t;
+        }
+    }
+    c->pacc = saved;
+    c->prof = prof;
+    if (chosen) *chosen = best;
+    return select_variant(c, best);
 }
 
 int hawkes_profile_enable(hawkes_ctx* c, int on) {

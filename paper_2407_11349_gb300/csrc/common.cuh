@@ -12,34 +12,48 @@ namespace hk {
 
 // ---------------------------------------------------------------------------
 // Tiling of the N x N pair matrix.
-//   A warp owns WROWS = 32 * R rows (R per lane, strided by 32), a CTA owns
-//   TR = WARPS * WROWS rows.  Source (column) events are streamed through
-//   shared memory in tiles of TC events, one TMA bulk copy each.  Times are
-//   stored relative to the first event of their block of TB = TC events.
+//   A CTA has WARPS warps; a warp owns 32 x R rows (R per lane, strided by 32,
+//   R a kernel-variant parameter).  Source (column) events are streamed
+//   through shared memory in tiles of TC events, one TMA bulk copy each, and
+//   a work item covers up to CHUNK consecutive tiles.  Times are stored
+//   relative to the first event of their block of TB = TC events.  Event
+//   arrays are padded to a multiple of NPAD_MULT (the largest row tile).
 // ---------------------------------------------------------------------------
-constexpr int R = 4;
 constexpr int WARPS = 8;
 constexpr int THREADS = WARPS * 32;
-constexpr int WROWS = 32 * R;
-constexpr int TR = WARPS * WROWS;
 constexpr int TC = 256;
 constexpr int TB = TC;
+constexpr int CHUNK = 16;
+constexpr int NPAD_MULT = 2048;
 static_assert(TC == THREADS, "column flush maps one thread to one column");
-static_assert(TB % WROWS == 0, "a warp's rows share one time block");
-static_assert(TR % TC == 0, "row tiles are whole column tiles");
 
-// Staged per-event record (32 B), rebuilt every call from the FP64 inputs
-// and the parameters.  Coordinates are pre-scaled so that a background
-// exponent is -(r~^2 + dt~^2) in base 2:
-//   x~ = x sqrt(a_x), a_x = log2(e) / (2 tau_x^2)   split hi + lo in FP32
+// Staged per-event record (64 B), rebuilt every call from the FP64 inputs and
+// the parameters.  Values are negated and duplicated so that a packed f32x2
+// add with a pair of rows forms both differences:
+//   q0 = (-t~, -t~, -xh, -xh)   q1 = (-xl, -xl, -yh, -yh)
+//   q2 = (-yl, -yl, -beta, -beta)   q3 = (ce, ce, 0, 0)
+// with coordinates pre-scaled so that a background exponent is
+// -(r~^2 + dt~^2) in base 2:
+//   x~ = x sqrt(a_x), a_x = log2(e) / (2 tau_x^2), split hi + lo in FP32
 //   t~ = (t - T_block) sqrt(a_t), a_t = log2(e) / (2 tau_t^2)
 //   beta = tau_x^2 / (h^2 s^2)    (excitation spatial exponent is beta r~^2)
 //   ce = -2 log2(s)               (the 1 / s^2 of the source's density)
-struct __align__(16) Ev {
-    float t, xh, yh, beta;
-    float xl, yl, ce, pad;
+// In device memory the records of each tile of TC events are stored as four
+// planes, q0[TC] q1[TC] q2[TC] q3[TC], so that lanes reading consecutive
+// events touch consecutive 16-byte words (no shared-memory bank conflicts);
+// one tile is one contiguous 64 x TC-byte block for the TMA copy.
+struct __align__(16) Rec {
+    float v[16];
 };
-static_assert(sizeof(Ev) == 32, "Ev is two 16-byte vectors");
+static_assert(sizeof(Rec) == 64, "Rec is four 16-byte vectors");
+
+// Address of plane q of event e's record in the tiled layout.
+__host__ __device__ __forceinline__ float4* rec_q(Rec* base, int64_t e, int q) {
+    return reinterpret_cast<float4*>(base) + (e / TC) * 4 * TC + q * TC + (e % TC);
+}
+__host__ __device__ __forceinline__ const float4* rec_q(const Rec* base, int64_t e, int q) {
+    return reinterpret_cast<const float4*>(base) + (e / TC) * 4 * TC + q * TC + (e % TC);
+}
 
 // Time value given to padding events: far after every real event, so that
 // every pair term with a padding event is exactly 0 (and finite products).
@@ -154,7 +168,6 @@ struct hawkes_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int sms = 0;
-    int sweep_grid = 0;
 
     int64_t n = 0, npad = 0;
     int32_t n_counties = 0;
@@ -169,7 +182,12 @@ struct hawkes_ctx {
     int32_t* lo = nullptr;     // [npad] first index with t_j == t_i
     int32_t* hi = nullptr;     // [npad] one past the last index with t_j == t_i
     double* tb = nullptr;      // [npad / TB] block time bases
-    hk::Ev* ev = nullptr;      // [npad] staged FP32 records
+    hk::Rec* rec = nullptr;    // [npad] staged FP32 records
+    int4* items = nullptr;     // symmetric-sweep work list
+    int nitems = 0;
+    int items_variant = -1;    // variant the work list was built for
+    int variant = 0;           // sweep kernel variant in use
+    int variant_bpsm = 1;      // its resident CTAs per SM
     double* acc = nullptr;     // [6 * npad] per-row moment sums (natural units)
     double* partials = nullptr;// [final_blocks * 8]
     double* fix7 = nullptr;    // [8] sums over FP64-recomputed rows

@@ -96,7 +96,7 @@ __device__ __forceinline__ Consts make_consts(const hawkes_params* P) {
 __global__ void k_prep(const double* __restrict__ t, const double* __restrict__ x,
                        const double* __restrict__ y, const double* __restrict__ s,
                        const double* __restrict__ tb, const hawkes_params* P, int model1,
-                       int stage, int64_t n, int64_t npad, Ev* __restrict__ ev,
+                       int stage, int64_t n, int64_t npad, Rec* __restrict__ rec,
                        double* __restrict__ acc, double* __restrict__ cc, int* ctr,
                        double* fix7) {
     const Consts k = make_consts(P);
@@ -123,27 +123,29 @@ __global__ void k_prep(const double* __restrict__ t, const double* __restrict__ 
 #pragma unroll
         for (int q = 0; q < 6; ++q) acc[q * npad + e] = 0.0;
         if (!stage) continue;
-        Ev r;
+        float nt, nxh, nxl, nyh, nyl, nb, ce;
         if (e < n) {
             const double tt = (t[e] - tb[e / TB]) * k.kt;
             const double xs = x[e] * k.kx, ys = y[e] * k.kx;
             const float xh = static_cast<float>(xs), yh = static_cast<float>(ys);
             const double se = model1 ? 1.0 : s[e];
-            r.t = static_cast<float>(tt);
-            r.xh = xh;
-            r.yh = yh;
-            r.xl = static_cast<float>(xs - static_cast<double>(xh));
-            r.yl = static_cast<float>(ys - static_cast<double>(yh));
-            r.beta = static_cast<float>(beta0 / (se * se));
-            r.ce = static_cast<float>(-2.0 * log2(se));
+            nt = -static_cast<float>(tt);
+            nxh = -xh;
+            nyh = -yh;
+            nxl = -static_cast<float>(xs - static_cast<double>(xh));
+            nyl = -static_cast<float>(ys - static_cast<double>(yh));
+            nb = -static_cast<float>(beta0 / (se * se));
+            ce = static_cast<float>(-2.0 * log2(se));
         } else {
-            r.t = PAD_T;
-            r.xh = r.yh = r.xl = r.yl = 0.f;
-            r.beta = 0.f;
-            r.ce = 0.f;
+            nt = -PAD_T;
+            nxh = nyh = nxl = nyl = 0.f;
+            nb = 0.f;
+            ce = 0.f;
         }
-        r.pad = 0.f;
-        ev[e] = r;
+        *rec_q(rec, e, 0) = make_float4(nt, nt, nxh, nxh);
+        *rec_q(rec, e, 1) = make_float4(nxl, nxl, nyh, nyh);
+        *rec_q(rec, e, 2) = make_float4(nyl, nyl, nb, nb);
+        *rec_q(rec, e, 3) = make_float4(ce, ce, 0.f, 0.f);
     }
 }
 

@@ -3,116 +3,167 @@
 //
 // For every ordered pair (target i, source j) the model has a background term
 // (if t_j != t_i) and an excitation term (if t_j < t_i); see Sec. 2.1, eqs.
-// 2-3.  With the parameters mu, theta and the normalising constants factored
-// out, each row needs
+// 2-3.  With mu, theta and the normalising constants factored out, each row
+// needs
 //   SB = sum B',  SBr = sum B' r^2,  SBt = sum B' dt^2       B' = exp(-r^2/2tau_x^2 - dt^2/2tau_t^2)
 //   SE = sum E',  SEt = sum E' dt,   SEq = sum E' r^2/s_j^2  E' = s_j^-2 exp(-omega dt - r^2/2h^2 s_j^2)
 // from which lambda_i and its six partial derivatives follow in closed form.
 //
 // Symmetric mode (the whole sum): B' is symmetric in (i, j), so each unordered
 // pair j < i is visited once and its B' is added to both row i and row j.  A
-// warp holds 32 x R rows in registers; the 32 lanes walk a chunk of 32 source
-// columns in rotated order (lane k takes column (k + step) mod 32), so the
-// column partial sums travel around the warp by one shuffle per step and end
-// at their column's lane.  Tie and triangle masks use the index range
-// [lo_i, hi_i) of events with t_j == t_i, computed in FP64 from the sorted
-// times, so FP32 rounding never changes an indicator.
+// warp holds 32 x R rows in registers, two rows per packed f32x2 register
+// pair, so every pair operation is one FFMA2/FADD2/FMUL2 for two rows.  The
+// 32 lanes walk a chunk of 32 source columns in rotated order (lane k takes
+// column (k + step) mod 32), so the column partial sums travel around the
+// warp by one shuffle per step and end at their column's lane.  Source
+// records hold negated, duplicated values, so every difference is a packed
+// add with the column value already in both halves.
+//
+// Tie and triangle masks use the index range [lo_i, hi_i) of events with
+// t_j == t_i, computed in FP64 from the sorted times, so FP32 rounding never
+// changes an indicator.
 //
 // Window mode (rows [row_begin, row_end) only, Sec. 2.3.2): every row sweeps
 // all sources without the symmetric shortcut.
 //
-// Precision: pair terms in FP32 with exp2 on the SFU; per-row partials are
-// folded into FP64 after every 256-column tile; column partials are added to
-// FP64 accumulators per tile.
+// Work is split into items (row tile x chunk of column tiles) taken from an
+// atomic queue, longest first.  Pair terms are FP32 with exp2 on the SFU;
+// row sums are FP32 within an item (CHUNK x TC sources) and FP64 across
+// items; column sums are FP32 within a tile and FP64 across tiles.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace hk {
 
 enum { M_NONE = 0, M_LOWER = 1, M_TWO = 2 };
 
-struct RowRegs {
-    float t0[R], tp[R], xh[R], xl[R], yh[R], yl[R];
-    int lo[R], hi[R];
-    float sB[R], sBr[R], sBt[R], sE[R], sEt[R], sEq[R];
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int RP>
+struct Rows {
+    float2 tp[RP], xh[RP], xl[RP], yh[RP], yl[RP];
+    float2 sB[RP], sBr[RP], sBt[RP], sE[RP], sEt[RP], sEq[RP];
 };
 
-// One tile of TC source columns against the warp's rows.
+// One tile of TC source columns against the warp's 2 RP rows per lane.
 //   MASK   M_NONE: every pair valid; M_LOWER: valid iff j < lo_i (lower
-//          triangle without ties); M_TWO: background iff j < lo_i or j >= hi_i,
-//          excitation iff j < lo_i
+//          triangle without ties); M_TWO: background iff j < lo_i or
+//          j >= hi_i, excitation iff j < lo_i
 //   EXC    evaluate the excitation term (sources strictly earlier)
 //   COL    also accumulate the background into the source columns
-template <int MASK, bool EXC, bool COL>
-__device__ __forceinline__ void tile_pass(const Ev* __restrict__ tile, int j0, int lane,
-                                          RowRegs& rr, float om_t, float* __restrict__ colacc) {
+// rlo/rhi: shared-memory lo/hi of the lane's rows (masked tiles only).
+template <int RP, int MASK, bool EXC, bool COL>
+__device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j0, int lane,
+                                          Rows<RP>& rr, float2 nomt,
+                                          const int* __restrict__ rlo,
+                                          const int* __restrict__ rhi, float* __restrict__ colacc) {
 #pragma unroll 1
     for (int ch = 0; ch < TC / 32; ++ch) {
-        float cB = 0.f, cBr = 0.f, cBt = 0.f;
+        float2 cB = f2(0.f, 0.f), cBr = f2(0.f, 0.f), cBt = f2(0.f, 0.f);
 #pragma unroll 2
         for (int s = 0; s < 32; ++s) {
             const int c = ch * 32 + ((lane + s) & 31);
-            const float4 a = reinterpret_cast<const float4*>(tile + c)[0];  // t, xh, yh, beta
-            const float4 b = reinterpret_cast<const float4*>(tile + c)[1];  // xl, yl, ce, -
+            const float4 q0 = tile[0 * TC + c];  // -t, -t, -xh, -xh
+            const float4 q1 = tile[1 * TC + c];  // -xl, -xl, -yh, -yh
+            const float4 q2 = tile[2 * TC + c];  // -yl, -yl, -beta, -beta
+            const float4 q3 = tile[3 * TC + c];  // ce, ce, -, -
+            const float2 nT = f2(q0.x, q0.y), nXH = f2(q0.z, q0.w);
+            const float2 nXL = f2(q1.x, q1.y), nYH = f2(q1.z, q1.w);
+            const float2 nYL = f2(q2.x, q2.y), NB = f2(q2.z, q2.w);
+            const float2 CE = f2(q3.x, q3.y);
             const int j = j0 + c;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float dt = rr.tp[r] - a.x;
-                const float dx = (rr.xh[r] - a.y) + (rr.xl[r] - b.x);
-                const float dy = (rr.yh[r] - a.z) + (rr.yl[r] - b.y);
-                const float r2 = fmaf(dy, dy, dx * dx);
-                const float dt2 = dt * dt;
-                float B = ex2(-(dt2 + r2));
-                if (MASK == M_LOWER) B = (j < rr.lo[r]) ? B : 0.f;
-                if (MASK == M_TWO) B = (j < rr.lo[r] || j >= rr.hi[r]) ? B : 0.f;
-                rr.sB[r] += B;
-                rr.sBr[r] = fmaf(B, r2, rr.sBr[r]);
-                rr.sBt[r] = fmaf(B, dt2, rr.sBt[r]);
+            for (int p = 0; p < RP; ++p) {
+                const float2 dt = add2(rr.tp[p], nT);
+                const float2 dx = add2(add2(rr.xh[p], nXH), add2(rr.xl[p], nXL));
+                const float2 dy = add2(add2(rr.yh[p], nYH), add2(rr.yl[p], nYL));
+                const float2 r2 = fma2(dy, dy, mul2(dx, dx));
+                const float2 dt2 = mul2(dt, dt);
+                const float2 aB = add2(dt2, r2);
+                float2 B = f2(ex2(-aB.x), ex2(-aB.y));
+                if (MASK != M_NONE) {
+                    const int l0 = rlo[2 * p], l1 = rlo[2 * p + 1];
+                    if (MASK == M_LOWER) {
+                        B.x = (j < l0) ? B.x : 0.f;
+                        B.y = (j < l1) ? B.y : 0.f;
+                    } else {
+                        B.x = (j < l0 || j >= rhi[2 * p]) ? B.x : 0.f;
+                        B.y = (j < l1 || j >= rhi[2 * p + 1]) ? B.y : 0.f;
+                    }
+                }
+                rr.sB[p] = add2(rr.sB[p], B);
+                rr.sBr[p] = fma2(B, r2, rr.sBr[p]);
+                rr.sBt[p] = fma2(B, dt2, rr.sBt[p]);
                 if (COL) {
-                    cB += B;
-                    cBr = fmaf(B, r2, cBr);
-                    cBt = fmaf(B, dt2, cBt);
+                    cB = add2(cB, B);
+                    cBr = fma2(B, r2, cBr);
+                    cBt = fma2(B, dt2, cBt);
                 }
                 if (EXC) {
-                    const float v = a.w * r2;
-                    float E = ex2(b.z - fmaf(om_t, dt, v));
-                    if (MASK != M_NONE) E = (j < rr.lo[r]) ? E : 0.f;
-                    rr.sE[r] += E;
-                    rr.sEt[r] = fmaf(E, dt, rr.sEt[r]);
-                    rr.sEq[r] = fmaf(E, v, rr.sEq[r]);
+                    const float2 nv = mul2(NB, r2);                  // -beta r~^2
+                    const float2 arg = add2(fma2(nomt, dt, nv), CE); // ce - omega~ dt - beta r~^2
+                    float2 E = f2(ex2(arg.x), ex2(arg.y));
+                    if (MASK != M_NONE) {
+                        E.x = (j < rlo[2 * p]) ? E.x : 0.f;
+                        E.y = (j < rlo[2 * p + 1]) ? E.y : 0.f;
+                    }
+                    rr.sE[p] = add2(rr.sE[p], E);
+                    rr.sEt[p] = fma2(E, dt, rr.sEt[p]);
+                    rr.sEq[p] = fma2(E, nv, rr.sEq[p]);  // accumulates -sum E beta r~^2
                 }
             }
             if (COL) {
                 const int src = (lane + 1) & 31;
-                cB = __shfl_sync(0xffffffffu, cB, src);
-                cBr = __shfl_sync(0xffffffffu, cBr, src);
-                cBt = __shfl_sync(0xffffffffu, cBt, src);
+                cB.x = __shfl_sync(0xffffffffu, cB.x, src);
+                cB.y = __shfl_sync(0xffffffffu, cB.y, src);
+                cBr.x = __shfl_sync(0xffffffffu, cBr.x, src);
+                cBr.y = __shfl_sync(0xffffffffu, cBr.y, src);
+                cBt.x = __shfl_sync(0xffffffffu, cBt.x, src);
+                cBt.y = __shfl_sync(0xffffffffu, cBt.y, src);
             }
         }
         if (COL) {  // lane k now holds column ch*32 + k, summed over the warp's rows
-            atomicAdd(colacc + 0 * TC + ch * 32 + lane, cB);
-            atomicAdd(colacc + 1 * TC + ch * 32 + lane, cBr);
-            atomicAdd(colacc + 2 * TC + ch * 32 + lane, cBt);
+            atomicAdd(colacc + 0 * TC + ch * 32 + lane, cB.x + cB.y);
+            atomicAdd(colacc + 1 * TC + ch * 32 + lane, cBr.x + cBr.y);
+            atomicAdd(colacc + 2 * TC + ch * 32 + lane, cBt.x + cBt.y);
         }
     }
 }
 
-constexpr size_t SMEM_TILES = 2 * TC * sizeof(Ev);
-constexpr size_t SMEM_COLACC = 2 * 3 * TC * sizeof(float);
-constexpr size_t SMEM_ROWACC = 6 * R * THREADS * sizeof(double);
-constexpr size_t SWEEP_SMEM = SMEM_TILES + SMEM_COLACC + SMEM_ROWACC;
+template <int RP>
+struct Geo {
+    static constexpr int R = 2 * RP;          // rows per lane
+    static constexpr int WROWS = 32 * R;      // rows per warp
+    static constexpr int TR = WARPS * WROWS;  // rows per row tile
+    static_assert(TB % WROWS == 0, "a warp's rows share one time block");
+    static constexpr size_t SMEM_TILES = 2 * TC * sizeof(Rec);
+    static constexpr size_t SMEM_COLACC = 2 * 3 * TC * sizeof(float);
+    static constexpr size_t SMEM_LOHI = 2 * THREADS * R * sizeof(int);
+    static constexpr size_t SMEM = SMEM_TILES + SMEM_COLACC + SMEM_LOHI;
+};
 
-// Persistent sweep.  Work item = one row tile of TR rows; SYM takes them
-// largest first (row tile I has I + 1 column-tile strips of work).
-template <bool SYM>
-__global__ void __launch_bounds__(THREADS, 2)
-    k_sweep(const Ev* __restrict__ ev, const int32_t* __restrict__ lo,
+// Persistent sweep over work items.
+//   SYM: item k = items[k] = (row tile, first column tile, end column tile)
+//   window: item k -> row tile item0 + k / nch, column chunk k % nch
+template <int RP, int MINB, bool SYM>
+__global__ void __launch_bounds__(THREADS, MINB)
+    k_sweep(const Rec* __restrict__ rec, const int32_t* __restrict__ lo,
             const int32_t* __restrict__ hi, const double* __restrict__ tb,
             const double* __restrict__ cc, double* __restrict__ acc, int* __restrict__ ctr,
-            int64_t n, int64_t npad, int64_t row_begin, int64_t row_end, int nitems, int item0) {
+            const int4* __restrict__ items, int nitems, int64_t n, int64_t npad,
+            int64_t row_begin, int64_t row_end, int item0, int nch) {
+    using G = Geo<RP>;
+    constexpr int R = G::R;
     extern __shared__ __align__(128) unsigned char smem[];
-    Ev* tiles = reinterpret_cast<Ev*>(smem);
-    float* colacc = reinterpret_cast<float*>(smem + SMEM_TILES);
-    double* racc = reinterpret_cast<double*>(smem + SMEM_TILES + SMEM_COLACC);
+    Rec* tiles = reinterpret_cast<Rec*>(smem);
+    float* colacc = reinterpret_cast<float*>(smem + G::SMEM_TILES);
+    int* slo = reinterpret_cast<int*>(smem + G::SMEM_TILES + G::SMEM_COLACC);
+    int* shi = slo + THREADS * R;
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_item, s_abort;
 
@@ -127,46 +178,66 @@ __global__ void __launch_bounds__(THREADS, 2)
     for (int k = tid; k < 2 * 3 * TC; k += THREADS) colacc[k] = 0.f;
     __syncthreads();
 
-    const float om_t = static_cast<float>(cc[CC_OMT]);
+    const float omt = static_cast<float>(cc[CC_OMT]);
+    const float2 nomt = f2(-omt, -omt);
     const double kt = cc[CC_KT];
     const double sr = cc[CC_SR], st = cc[CC_ST], set = cc[CC_SET], seq = cc[CC_SEQ];
     const int ncol_tiles = static_cast<int>((n + TC - 1) / TC);
     uint32_t parbits = 0u;   // bit b: parity of the next phase of buffer b
     uint32_t pendbits = 0u;  // thread 0, bit b: a copy into buffer b is in flight
+    int* mylo = slo + tid * R;
+    int* myhi = shi + tid * R;
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(ctr + CT_WORK, 1);
         __syncthreads();
         const int item = s_item;
         if (item >= nitems || s_abort) break;
-        const int64_t I = SYM ? static_cast<int64_t>(nitems - 1 - item) : item0 + item;
-        const int64_t rc0 = I * TR;
-        const int64_t r0 = rc0 + warp * WROWS;
-        const int nJ = SYM ? static_cast<int>((min(rc0 + TR, n) + TC - 1) / TC) : ncol_tiles;
-
-        RowRegs rr;
+        int64_t I;
+        int jb, je;
+        if (SYM) {
+            const int4 it = items[item];
+            I = it.x;
+            jb = it.y;
+            je = it.z;
+        } else {
+            I = item0 + item / nch;
+            jb = (item % nch) * CHUNK;
+            je = min(jb + CHUNK, ncol_tiles);
+        }
+        const int64_t r0 = I * G::TR + warp * G::WROWS;  // warp's first row
         bool live = r0 < n;
-        if (!SYM) live = live && r0 < row_end && r0 + WROWS > row_begin;
+        if (!SYM) live = live && r0 < row_end && r0 + G::WROWS > row_begin;
+
+        Rows<RP> rr;
+        float t0[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int64_t i = r0 + lane + 32 * r;
-            const Ev e = ev[i];
-            rr.t0[r] = e.t;
-            rr.xh[r] = e.xh; rr.xl[r] = e.xl;
-            rr.yh[r] = e.yh; rr.yl[r] = e.yl;
-            rr.lo[r] = lo[i];
-            rr.hi[r] = hi[i];
-            rr.sB[r] = rr.sBr[r] = rr.sBt[r] = rr.sE[r] = rr.sEt[r] = rr.sEq[r] = 0.f;
+        for (int p = 0; p < RP; ++p) {
+            const int64_t i0 = r0 + lane + 64 * p, i1 = i0 + 32;
+            const float4 a0 = *rec_q(rec, i0, 0), b0 = *rec_q(rec, i0, 1), c0 = *rec_q(rec, i0, 2);
+            const float4 a1 = *rec_q(rec, i1, 0), b1 = *rec_q(rec, i1, 1), c1 = *rec_q(rec, i1, 2);
+            t0[2 * p] = -a0.x;
+            t0[2 * p + 1] = -a1.x;
+            rr.xh[p] = f2(-a0.z, -a1.z);
+            rr.xl[p] = f2(-b0.x, -b1.x);
+            rr.yh[p] = f2(-b0.z, -b1.z);
+            rr.yl[p] = f2(-c0.x, -c1.x);
+            rr.sB[p] = rr.sBr[p] = rr.sBt[p] = rr.sE[p] = rr.sEt[p] = rr.sEq[p] = f2(0.f, 0.f);
+            mylo[2 * p] = lo[i0];
+            mylo[2 * p + 1] = lo[i1];
+            myhi[2 * p] = hi[i0];
+            myhi[2 * p + 1] = hi[i1];
         }
         const int lo_first = live ? lo[r0] : 0;
-        const int hi_last = live ? hi[min(r0 + WROWS, n) - 1] : 0;
+        const int hi_last = live ? hi[min(r0 + G::WROWS, n) - 1] : 0;
         const double trow = tb[r0 / TB];
-        for (int k = 0; k < 6 * R; ++k) racc[k * THREADS + tid] = 0.0;
+        const int nJ = je - jb;
 
         if (tid == 0) {
             for (int q = 0; q < 2 && q < nJ; ++q) {
-                mbar_arrive_expect_tx(&bars[q], TC * sizeof(Ev));
-                tma_load_1d(tiles + q * TC, ev + static_cast<int64_t>(q) * TC, TC * sizeof(Ev), &bars[q]);
+                mbar_arrive_expect_tx(&bars[q], TC * sizeof(Rec));
+                tma_load_1d(tiles + q * TC, rec + static_cast<int64_t>(jb + q) * TC,
+                            TC * sizeof(Rec), &bars[q]);
                 pendbits |= 1u << q;
             }
         }
@@ -179,45 +250,35 @@ __global__ void __launch_bounds__(THREADS, 2)
             }
             parbits ^= 1u << buf;
             pendbits &= ~(1u << buf);
-            const int j0 = J * TC;
+            const int jt = jb + J;
+            const int j0 = jt * TC;
             if (live) {
-                const float dT = static_cast<float>((trow - tb[J]) * kt);
+                const float dT = static_cast<float>((trow - tb[jt]) * kt);
 #pragma unroll
-                for (int r = 0; r < R; ++r) rr.tp[r] = rr.t0[r] + dT;
-                const Ev* tile = tiles + buf * TC;
+                for (int p = 0; p < RP; ++p) rr.tp[p] = f2(t0[2 * p] + dT, t0[2 * p + 1] + dT);
+                const float4* tile = reinterpret_cast<const float4*>(tiles + buf * TC);
                 float* ca = colacc + buf * 3 * TC;
                 if (SYM) {
-                    if (j0 < r0 + WROWS) {
+                    if (j0 < r0 + G::WROWS) {
                         if (j0 + TC > lo_first)
-                            tile_pass<M_LOWER, true, true>(tile, j0, lane, rr, om_t, ca);
+                            tile_pass<RP, M_LOWER, true, true>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                         else
-                            tile_pass<M_NONE, true, true>(tile, j0, lane, rr, om_t, ca);
+                            tile_pass<RP, M_NONE, true, true>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                     }
                 } else {
                     if (j0 + TC <= lo_first)
-                        tile_pass<M_NONE, true, false>(tile, j0, lane, rr, om_t, ca);
+                        tile_pass<RP, M_NONE, true, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                     else if (j0 >= hi_last)
-                        tile_pass<M_NONE, false, false>(tile, j0, lane, rr, om_t, ca);
+                        tile_pass<RP, M_NONE, false, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                     else
-                        tile_pass<M_TWO, true, false>(tile, j0, lane, rr, om_t, ca);
-                }
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    double* q = racc + r * THREADS + tid;
-                    q[0 * R * THREADS] += static_cast<double>(rr.sB[r]);
-                    q[1 * R * THREADS] += static_cast<double>(rr.sBr[r]);
-                    q[2 * R * THREADS] += static_cast<double>(rr.sBt[r]);
-                    q[3 * R * THREADS] += static_cast<double>(rr.sE[r]);
-                    q[4 * R * THREADS] += static_cast<double>(rr.sEt[r]);
-                    q[5 * R * THREADS] += static_cast<double>(rr.sEq[r]);
-                    rr.sB[r] = rr.sBr[r] = rr.sBt[r] = rr.sE[r] = rr.sEt[r] = rr.sEq[r] = 0.f;
+                        tile_pass<RP, M_TWO, true, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                 }
             }
             __syncthreads();
             if (tid == 0 && J + 2 < nJ && !s_abort) {
-                mbar_arrive_expect_tx(&bars[buf], TC * sizeof(Ev));
-                tma_load_1d(tiles + buf * TC, ev + static_cast<int64_t>(J + 2) * TC, TC * sizeof(Ev),
-                            &bars[buf]);
+                mbar_arrive_expect_tx(&bars[buf], TC * sizeof(Rec));
+                tma_load_1d(tiles + buf * TC, rec + static_cast<int64_t>(jt + 2) * TC,
+                            TC * sizeof(Rec), &bars[buf]);
                 pendbits |= 1u << buf;
             }
             if (SYM) {
@@ -238,23 +299,28 @@ __global__ void __launch_bounds__(THREADS, 2)
 
         if (live && !s_abort) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int64_t i = r0 + lane + 32 * r;
-                if (i >= n || (!SYM && (i < row_begin || i >= row_end))) continue;
-                const double* q = racc + r * THREADS + tid;
-                const double vB = q[0], vBr = q[1 * R * THREADS] * sr, vBt = q[2 * R * THREADS] * st;
-                if (SYM) {
-                    atomicAdd(acc + 0 * npad + i, vB);
-                    atomicAdd(acc + 1 * npad + i, vBr);
-                    atomicAdd(acc + 2 * npad + i, vBt);
-                } else {
-                    acc[0 * npad + i] = vB;
-                    acc[1 * npad + i] = vBr;
-                    acc[2 * npad + i] = vBt;
+            for (int p = 0; p < RP; ++p) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t i = r0 + lane + 64 * p + 32 * h;
+                    if (i >= n || (!SYM && (i < row_begin || i >= row_end))) continue;
+                    const float vB = h ? rr.sB[p].y : rr.sB[p].x;
+                    const float vBr = h ? rr.sBr[p].y : rr.sBr[p].x;
+                    const float vBt = h ? rr.sBt[p].y : rr.sBt[p].x;
+                    const float vE = h ? rr.sE[p].y : rr.sE[p].x;
+                    const float vEt = h ? rr.sEt[p].y : rr.sEt[p].x;
+                    const float vEq = h ? rr.sEq[p].y : rr.sEq[p].x;
+                    if (vB != 0.f || vBr != 0.f || vBt != 0.f) {
+                        atomicAdd(acc + 0 * npad + i, static_cast<double>(vB));
+                        atomicAdd(acc + 1 * npad + i, static_cast<double>(vBr) * sr);
+                        atomicAdd(acc + 2 * npad + i, static_cast<double>(vBt) * st);
+                    }
+                    if (vE != 0.f || vEt != 0.f || vEq != 0.f) {
+                        atomicAdd(acc + 3 * npad + i, static_cast<double>(vE));
+                        atomicAdd(acc + 4 * npad + i, static_cast<double>(vEt) * set);
+                        atomicAdd(acc + 5 * npad + i, -static_cast<double>(vEq) * seq);
+                    }
                 }
-                acc[3 * npad + i] = q[3 * R * THREADS];
-                acc[4 * npad + i] = q[4 * R * THREADS] * set;
-                acc[5 * npad + i] = q[5 * R * THREADS] * seq;
             }
         }
         __syncthreads();
@@ -267,46 +333,88 @@ __global__ void __launch_bounds__(THREADS, 2)
             if ((pendbits >> q) & 1u) (void)mbar_wait(&bars[q], (parbits >> q) & 1u);
 }
 
-}  // namespace hk
+// ---------------------------------------------------------------------------
+// Host side: kernel variants, their work lists, and launch.
+// ---------------------------------------------------------------------------
+using SweepFn = void (*)(const Rec*, const int32_t*, const int32_t*, const double*, const double*,
+                         double*, int*, const int4*, int, int64_t, int64_t, int64_t, int64_t, int,
+                         int);
 
-// Host-side launch helpers (called from api.cu).
-namespace hk {
+struct Variant {
+    int rp, minb;
+    SweepFn sym, win;
+    size_t smem;
+    int tr;
+};
+
+static const Variant kVariants[] = {
+    {4, 1, k_sweep<4, 1, true>, k_sweep<4, 1, false>, Geo<4>::SMEM, Geo<4>::TR},
+    {2, 2, k_sweep<2, 2, true>, k_sweep<2, 2, false>, Geo<2>::SMEM, Geo<2>::TR},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int sweep_num_variants() { return kNumVariants; }
+int sweep_variant_rows(int v) { return kVariants[v].tr; }
 
 cudaError_t sweep_setup_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(SWEEP_SMEM));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(SWEEP_SMEM));
+    for (const auto& v : kVariants) {
+        cudaError_t e = cudaFuncSetAttribute(v.sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(v.smem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(v.win, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(v.smem));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-int sweep_blocks_per_sm() {
+int sweep_blocks_per_sm(int v) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep<true>, THREADS, SWEEP_SMEM) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kVariants[v].sym, THREADS,
+                                                      kVariants[v].smem) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end) {
-    int nitems, item0;
-    if (sym) {
-        nitems = static_cast<int>(c->npad / TR);
-        item0 = 0;
-    } else {
-        item0 = static_cast<int>(row_begin / TR);
-        nitems = static_cast<int>((row_end + TR - 1) / TR) - item0;
+// Symmetric work list for n events and variant v: (row tile, column tiles
+// [jb, je)) in chunks of CHUNK tiles, longest first.
+std::vector<int4> sweep_items(int64_t n, int v) {
+    const int tr = kVariants[v].tr;
+    const int64_t nI = (n + tr - 1) / tr;
+    std::vector<int4> items;
+    for (int64_t I = 0; I < nI; ++I) {
+        const int nJ = static_cast<int>((std::min<int64_t>((I + 1) * tr, n) + TC - 1) / TC);
+        for (int jb = 0; jb < nJ; jb += CHUNK)
+            items.push_back(make_int4(static_cast<int>(I), jb, std::min(jb + CHUNK, nJ), 0));
     }
-    const int grid = nitems < c->sweep_grid ? nitems : c->sweep_grid;
-    if (grid <= 0) return cudaSuccess;
-    if (sym)
-        k_sweep<true><<<grid, THREADS, SWEEP_SMEM, c->stream>>>(c->ev, c->lo, c->hi, c->tb, c->cc,
-                                                                c->acc, c->ctr, c->n, c->npad,
-                                                                row_begin, row_end, nitems, item0);
-    else
-        k_sweep<false><<<grid, THREADS, SWEEP_SMEM, c->stream>>>(c->ev, c->lo, c->hi, c->tb, c->cc,
-                                                                 c->acc, c->ctr, c->n, c->npad,
-                                                                 row_begin, row_end, nitems, item0);
+    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) {
+        return (a.z - a.y) > (b.z - b.y) || ((a.z - a.y) == (b.z - b.y) && a.x > b.x);
+    });
+    return items;
+}
+
+cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end) {
+    const Variant& v = kVariants[c->variant];
+    const int grid_cap = c->sms * c->variant_bpsm;
+    if (sym) {
+        const int nitems = c->nitems;
+        const int grid = nitems < grid_cap ? nitems : grid_cap;
+        if (grid <= 0) return cudaSuccess;
+        v.sym<<<grid, THREADS, v.smem, c->stream>>>(c->rec, c->lo, c->hi, c->tb, c->cc, c->acc,
+                                                    c->ctr, c->items, nitems, c->n, c->npad,
+                                                    row_begin, row_end, 0, 0);
+    } else {
+        const int item0 = static_cast<int>(row_begin / v.tr);
+        const int nrt = static_cast<int>((row_end + v.tr - 1) / v.tr) - item0;
+        const int ncol = static_cast<int>((c->n + TC - 1) / TC);
+        const int nch = (ncol + CHUNK - 1) / CHUNK;
+        const int nitems = nrt * nch;
+        const int grid = nitems < grid_cap ? nitems : grid_cap;
+        if (grid <= 0) return cudaSuccess;
+        v.win<<<grid, THREADS, v.smem, c->stream>>>(c->rec, c->lo, c->hi, c->tb, c->cc, c->acc,
+                                                    c->ctr, nullptr, nitems, c->n, c->npad,
+                                                    row_begin, row_end, item0, nch);
+    }
     return cudaGetLastError();
 }
 

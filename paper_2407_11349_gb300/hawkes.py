@@ -60,6 +60,11 @@ _SIGS = {
     "hawkes_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hawkes_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_profile)]),
     "hawkes_num_events": (ctypes.c_int64, [_VP]),
+    "hawkes_sweep_variants": (ctypes.c_int, []),
+    "hawkes_set_sweep_variant": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "hawkes_get_sweep_variant": (ctypes.c_int, [_VP]),
+    "hawkes_tune": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_params), ctypes.c_uint32, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int), _D]),
 }
 
 
@@ -181,6 +186,30 @@ def hawkes_num_events(ctx):
     return int(lib().hawkes_num_events(ctx))
 
 
+def hawkes_sweep_variants():
+    return int(lib().hawkes_sweep_variants())
+
+
+def hawkes_set_sweep_variant(ctx, variant):
+    _check(lib().hawkes_set_sweep_variant(ctx, int(variant)), "hawkes_set_sweep_variant")
+
+
+def hawkes_get_sweep_variant(ctx):
+    return int(lib().hawkes_get_sweep_variant(ctx))
+
+
+def hawkes_tune(ctx, params, flags=HAWKES_F32, reps=2):
+    """Time every sweep variant on the current events; keep the fastest.
+    Returns (chosen index, mean sweep ms per variant)."""
+    nv = hawkes_sweep_variants()
+    ms = np.zeros(nv)
+    ch = ctypes.c_int(-1)
+    p = as_params(params)
+    _check(lib().hawkes_tune(ctx, ctypes.byref(p), int(flags), int(reps), ctypes.byref(ch), _dp(ms)),
+           "hawkes_tune")
+    return ch.value, ms
+
+
 # --- convenience wrapper ---------------------------------------------------
 
 class Hawkes:
@@ -232,6 +261,16 @@ class Hawkes:
         if on is not None:
             hawkes_profile_enable(self.ctx, on)
         return hawkes_profile_read(self.ctx)
+
+    def tune(self, params, flags=HAWKES_F32, reps=2):
+        return hawkes_tune(self.ctx, params, flags, reps)
+
+    def set_variant(self, v):
+        hawkes_set_sweep_variant(self.ctx, v)
+
+    @property
+    def variant(self):
+        return hawkes_get_sweep_variant(self.ctx)
 
     @property
     def n(self):

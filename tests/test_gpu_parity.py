@@ -95,6 +95,30 @@ def test_degenerate_and_other_parameters(hk, p):
     check_both(hk, small_grid(1800, seed=7), p=p, what=f"p={p}")
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+def test_sweep_variants_agree(hk, variant):
+    ds = small_grid(6000, seed=12)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle_rows(ds)
+    hk.set_variant(variant)
+    try:
+        ll, g = hk.loglik_grad(P0, HAWKES_F32)
+        assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, f"variant {variant}")
+        ll, g = hk.loglik_grad(P0, HAWKES_F32, 1000, 4500)
+        wref = oracle.loglik_grad(ds.t, ds.x, ds.y, P0, s=ds.s, row_begin=1000, row_end=4500)
+        assert_close(ll, g, wref, rows[1000:4500], TOL_LL32, TOL_G32, f"variant {variant} window")
+    finally:
+        hk.set_variant(0)
+
+
+def test_tune_picks_a_variant(hk):
+    ds = small_grid(20000, seed=13)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    chosen, ms = hk.tune(P0, reps=1)
+    assert 0 <= chosen < len(ms) and np.all(ms > 0) and ms[chosen] == ms.min()
+    hk.set_variant(0)
+
+
 def test_row_windows_sum_to_whole(hk):
     ds = small_grid(4100, seed=8)
     hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
@@ -122,8 +146,10 @@ def test_async_matches_sync(hk):
     hk.loglik_grad_async(dp.data_ptr(), dout.data_ptr(), HAWKES_F32)
     hk.profile()  # waits for the context stream
     o = dout.cpu().numpy()
-    assert abs(o[0] - ll) <= 1e-12 * abs(ll)
-    assert np.allclose(o[1:], g, rtol=1e-12, atol=0)
+    # FP32 partial sums are combined with atomics whose order varies from run
+    # to run, so repeated evaluations agree to the FP32 path's tolerance only
+    ref, rows = oracle_rows(ds)
+    assert_close(o[0], o[1:], np.concatenate([[ll], g]), rows, TOL_LL32, TOL_G32, "async vs sync")
 
 
 def test_resample_bit_exact(hk):
