@@ -57,7 +57,8 @@ enum {
     HAWKES_ERR_NONFINITE = -4,  /* a result was NaN or infinite */
     HAWKES_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
     HAWKES_ERR_OOM = -6,        /* device allocation failed */
-    HAWKES_ERR_STATE = -7       /* call out of order (e.g. no events set) */
+    HAWKES_ERR_STATE = -7,      /* call out of order (e.g. no events set) */
+    HAWKES_ERR_TOO_LARGE = -8   /* size above the fixed limit of hawkes_loglik_grad_noalloc */
 };
 
 /* Flags for the log-likelihood calls. */
@@ -201,6 +202,46 @@ int hawkes_tune(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags, in
 
 /* Number of events n of the current set (0 if none). */
 int64_t hawkes_num_events(const hawkes_ctx* ctx);
+
+/*
+ * Allocation-free log-likelihood and gradient (no counterpart in the paper;
+ * a deployment convenience of this library).
+ *
+ * For callers that cannot allocate device memory: code running inside a
+ * custom device allocator or memory-pool callback (a cudaMalloc there would
+ * recurse into the allocator), applications that reserve all device memory
+ * up front and account for every byte, and threads that must not block on
+ * the allocator's device-wide synchronisation.  This call allocates and frees
+ * nothing, on the device or through any library.  Its scratch space is one
+ * fixed array built into the library (about 10 MB), which every GPU that
+ * loads the library holds until the process exits.
+ *
+ *   d_t[n]        device pointer: event times, > 0, non-decreasing
+ *   d_x[n], d_y[n] device pointers: event locations
+ *   d_s[n]        device pointer: per-event source bandwidth scale s_j > 0
+ *                 (eq. 3), or NULL for s_j = 1 (eq. 2)
+ *   n             1 <= n <= HAWKES_NOALLOC_MAX_N (65,536); larger n returns
+ *                 HAWKES_ERR_TOO_LARGE
+ *   d_params      device pointer to one hawkes_params
+ *   flags         HAWKES_F32, optionally | HAWKES_MODEL1 (the FP64 path is
+ *                 not offered here)
+ *   d_out         device pointer to 7 doubles: ell, then the six partials
+ *   cuda_stream   cudaStream_t of the current device to queue the work on
+ *                 (NULL: the legacy default stream)
+ * Computes the same quantity as hawkes_loglik_grad (whole sum, FP32 pair
+ * terms) on the current CUDA device and returns without waiting.  Invalid
+ * events detected on the device (unsorted or non-positive times, non-finite
+ * values) make all 7 outputs NaN.  The first call on each device looks up the
+ * scratch array's device address and sets kernel attributes; make that first
+ * call before any stream capture.  All calls on a device share the scratch
+ * array, which keeps the previous call's contents (each call clears what must
+ * start at zero): calls whose work can overlap on the GPU, e.g. on two
+ * streams, race and must be serialised by the caller.
+ */
+#define HAWKES_NOALLOC_MAX_N 65536
+int hawkes_loglik_grad_noalloc(const double* d_t, const double* d_x, const double* d_y,
+                               const double* d_s, int64_t n, const hawkes_params* d_params,
+                               uint32_t flags, double* d_out, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -247,6 +247,7 @@ const char* hawkes_strerror(int status) {
         case HAWKES_ERR_TIMEOUT: return "a bounded device wait gave up";
         case HAWKES_ERR_OOM: return "device out of memory";
         case HAWKES_ERR_STATE: return "call out of order";
+        case HAWKES_ERR_TOO_LARGE: return "size above the fixed scratch limit of the allocation-free entry point";
         default: return "unknown status";
     }
 }

@@ -65,6 +65,8 @@ _SIGS = {
     "hawkes_get_sweep_variant": (ctypes.c_int, [_VP]),
     "hawkes_tune": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_params), ctypes.c_uint32, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int), _D]),
+    "hawkes_loglik_grad_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, _VP,
+                                                  ctypes.c_uint32, _VP, _VP]),
 }
 
 
@@ -208,6 +210,19 @@ def hawkes_tune(ctx, params, flags=HAWKES_F32, reps=2):
     _check(lib().hawkes_tune(ctx, ctypes.byref(p), int(flags), int(reps), ctypes.byref(ch), _dp(ms)),
            "hawkes_tune")
     return ch.value, ms
+
+
+HAWKES_NOALLOC_MAX_N = 65536
+
+
+def hawkes_loglik_grad_noalloc(d_t, d_x, d_y, d_s, n, d_params, flags, d_out, stream=0):
+    """Allocation-free evaluation for callers that cannot allocate device memory
+    (see include/hawkes.h).  All pointers are device addresses of the caller's
+    buffers (``d_s`` may be 0 for s_j = 1); queued on ``stream``, no wait."""
+    _check(lib().hawkes_loglik_grad_noalloc(_VP(int(d_t)), _VP(int(d_x)), _VP(int(d_y)),
+                                            _VP(int(d_s) or None), int(n), _VP(int(d_params)),
+                                            int(flags), _VP(int(d_out)), _VP(int(stream) or None)),
+           "hawkes_loglik_grad_noalloc")
 
 
 # --- convenience wrapper ---------------------------------------------------
