@@ -200,6 +200,70 @@ int hawkes_get_sweep_variant(const hawkes_ctx* ctx);
 int hawkes_tune(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags, int reps,
                 int* chosen, double* ms);
 
+/*
+ * Batched evaluation (many problems in one persistent launch).
+ *
+ * A batch groups P >= 1 contexts on one device, each with its own events
+ * (MCMC chains with their own locations and parameters, or regional subsets
+ * of uneven size).  One run resamples every problem's locations (if keys were
+ * given), stages them, sweeps the pairs of ALL problems in a single
+ * persistent kernel launch that takes work items (problem, row tile, column
+ * chunk) from one queue, longest first, and reduces each problem to its own 7
+ * outputs.  The paper ran its 30 chains as separate jobs (Sec. 3.2).
+ *
+ *   problems[P]        contexts with events set (and counties, if seeds are
+ *                      given); each may appear once; the batch keeps pointers
+ *                      to them, so destroy the batch before any of them, and
+ *                      do not change their events while the batch exists
+ *   seeds[P], streams[P]  resample keys of each problem (Philox key as in
+ *                      hawkes_resample_locations), or both NULL for no resample
+ *   flags              HAWKES_F32, optionally | HAWKES_MODEL1
+ *   cuda_stream        stream for the batch's work, or NULL for its own
+ */
+typedef struct hawkes_batch hawkes_batch;
+int hawkes_batch_create(hawkes_batch** out, hawkes_ctx* const* problems, int32_t n_problems,
+                        const uint64_t* seeds, const uint64_t* streams, uint32_t flags,
+                        void* cuda_stream);
+void hawkes_batch_destroy(hawkes_batch* batch);
+
+/*
+ * Queue one batched evaluation at resample iteration `iteration`.
+ *   d_params  device pointer to P hawkes_params (problem p uses d_params[p])
+ *   d_out     device pointer to 7 P doubles (problem p writes d_out[7p .. 7p+6])
+ * If the batch was captured with these same two pointers, the captured CUDA
+ * graph is launched; otherwise the kernels are queued one by one.  Returns
+ * without waiting; see hawkes_batch_wait.
+ */
+int hawkes_batch_run(hawkes_batch* batch, const hawkes_params* d_params, uint64_t iteration,
+                     double* d_out);
+
+/*
+ * Capture the whole evaluation (resample, staging, the single sweep launch,
+ * per-problem reductions) into a CUDA graph bound to d_params and d_out; later
+ * hawkes_batch_run calls with the same pointers replay it.  The iteration is
+ * read from device memory written just before each launch.
+ */
+int hawkes_batch_capture(hawkes_batch* batch, const hawkes_params* d_params, double* d_out);
+
+/* Wait for the batch's queued work; return the first latched device error. */
+int hawkes_batch_wait(hawkes_batch* batch);
+
+/*
+ * Autotune the batch over the sweep variant, the column-chunk length of a
+ * work item (16, 32 or 64 tiles of 256 sources) and the item order (0: all
+ * items longest first; 1: problem by problem, largest problem first, each
+ * longest first).  Each configuration's single sweep launch is timed `reps`
+ * times with CUDA events after a warm-up, at d_params / d_out (device
+ * pointers as for hawkes_batch_run); the fastest is kept.  Outputs
+ * (optional): the chosen variant, chunk length, order and mean sweep time in
+ * ms.  Drops a captured graph (capture again after tuning).
+ */
+int hawkes_batch_tune(hawkes_batch* batch, const hawkes_params* d_params, double* d_out, int reps,
+                      int* variant, int* chunk, int* order, double* best_ms);
+
+/* Select the sweep variant, chunk length and item order directly (drops a captured graph). */
+int hawkes_batch_set_config(hawkes_batch* batch, int variant, int chunk, int order);
+
 /* Number of events n of the current set (0 if none). */
 int64_t hawkes_num_events(const hawkes_ctx* ctx);
 

@@ -24,7 +24,8 @@ __global__ void k_tri_area(const double*, int32_t, double*);
 __global__ void k_tri_county(const int32_t*, int32_t, int32_t, double*, int32_t*, int32_t*, int*);
 __global__ void k_tri_check(const int32_t*, int32_t, int32_t, int*);
 __global__ void k_resample(const int32_t*, int64_t, const double*, const double*, const int32_t*,
-                           const int32_t*, uint64_t, uint64_t, uint64_t, double*, double*);
+                           const int32_t*, uint64_t, uint64_t, uint64_t, const uint64_t*, double*,
+                           double*);
 // sweep.cu
 cudaError_t sweep_setup_attributes();
 int sweep_num_variants();
@@ -435,7 +436,7 @@ int hawkes_resample_locations(hawkes_ctx* c, uint64_t seed, uint64_t stream, uin
     return timed(c, HAWKES_K_RESAMPLE, [&] {
         k_resample<<<grid_for(c, c->n), 256, 0, c->stream>>>(c->county, c->n, c->tri_xy, c->tri_cum,
                                                              c->cfirst, c->clast, seed, stream,
-                                                             iteration, c->x, c->y);
+                                                             iteration, nullptr, c->x, c->y);
     });
 }
 

@@ -1,0 +1,342 @@
+// Batched evaluation: many problems (MCMC chains with their own parameters
+// and location draws, and regional subsets of uneven size) in one persistent
+// pair-sweep launch, optionally captured with the per-problem O(N) kernels in
+// one CUDA graph.  The paper ran its 30 chains as separate cluster jobs
+// (Sec. 3.2); here they share one GPU and one work queue.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hk {
+__global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
+                       const hawkes_params*, int, int, int64_t, int64_t, Rec*, double*, double*,
+                       int*, double*);
+__global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
+                           int, int*, int*, double*, double*);
+__global__ void k_rows64(const double*, const double*, const double*, const double*,
+                         const int32_t*, const int32_t*, const double*, int, int64_t, int64_t,
+                         int64_t, int64_t, int, const int*, int*, double*, double*, double*);
+__global__ void k_reduce(const double*, int, const double*, const double*, double*, int*);
+__global__ void k_resample(const int32_t*, int64_t, const double*, const double*, const int32_t*,
+                           const int32_t*, uint64_t, uint64_t, uint64_t, const uint64_t*, double*,
+                           double*);
+int sweep_num_variants();
+int sweep_blocks_per_sm(int v);
+std::vector<int4> sweep_items_batch(const std::vector<int64_t>& ns, int v, int chunk, int order);
+cudaError_t launch_sweep_batch(cudaStream_t st, int variant, int grid, const ProbDesc* probs,
+                               const int4* items, int nitems, int* ctr);
+
+__global__ void k_set_u64(uint64_t* dst, uint64_t v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
+}
+}  // namespace hk
+
+using namespace hk;
+
+struct hawkes_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 0;
+    uint32_t flags = 0;
+    std::vector<hawkes_ctx*> probs;
+    std::vector<uint64_t> seeds, streams;
+    bool resample = false;
+    ProbDesc* d_probs = nullptr;
+    int4* d_items = nullptr;
+    int nitems = 0;
+    int variant = 0;
+    int chunk = CHUNK;
+    int order = 1;
+    int grid = 0;
+    int* d_ctr = nullptr;        // [CT_COUNT]: work cursor, latched error
+    uint64_t* d_iter = nullptr;  // iteration read by the resample kernels
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const hawkes_params* g_params = nullptr;  // pointers the graph was captured with
+    double* g_out = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int st_of(cudaError_t e) {
+    if (e == cudaSuccess) return HAWKES_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? HAWKES_ERR_OOM : HAWKES_ERR_CUDA;
+}
+
+#define HB_TRY(expr)                       \
+    do {                                   \
+        int _rc = (expr);                  \
+        if (_rc != HAWKES_OK) return _rc;  \
+    } while (0)
+#define HB_CUDA(expr) HB_TRY(st_of(expr))
+
+void drop_graph(hawkes_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->g_params = nullptr;
+    b->g_out = nullptr;
+}
+
+int build_items(hawkes_batch* b, int variant, int chunk, int order) {
+    std::vector<int64_t> ns;
+    for (auto* c : b->probs) ns.push_back(c->n);
+    const std::vector<int4> items = sweep_items_batch(ns, variant, chunk, order);
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    HB_CUDA(cudaMalloc(&b->d_items, std::max<size_t>(items.size(), 1) * sizeof(int4)));
+    HB_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, b->stream));
+    HB_CUDA(cudaStreamSynchronize(b->stream));
+    b->nitems = static_cast<int>(items.size());
+    b->variant = variant;
+    b->chunk = chunk;
+    b->order = order;
+    b->grid = b->sms * sweep_blocks_per_sm(variant);
+    drop_graph(b);  // a captured graph refers to the old work list
+    return HAWKES_OK;
+}
+
+// Queue one batched evaluation.  d_params[P], d_out[7 P]; the iteration is read
+// from b->d_iter by the resample kernels.
+int enqueue(hawkes_batch* b, const hawkes_params* d_params, double* d_out, bool time_sweep) {
+    cudaStream_t st = b->stream;
+    const int model1 = (b->flags & HAWKES_MODEL1) ? 1 : 0;
+    const int P = static_cast<int>(b->probs.size());
+    for (int p = 0; p < P; ++p) {
+        hawkes_ctx* c = b->probs[p];
+        int g = static_cast<int>((c->npad + 255) / 256);
+        if (g > 8 * b->sms) g = 8 * b->sms;
+        if (b->resample)
+            k_resample<<<g, 256, 0, st>>>(c->county, c->n, c->tri_xy, c->tri_cum, c->cfirst, c->clast,
+                                          b->seeds[p], b->streams[p], 0, b->d_iter, c->x, c->y);
+        k_prep<<<g, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->tb, d_params + p, model1, 1, c->n,
+                                  c->npad, c->rec, c->acc, c->cc, c->ctr, c->fix7);
+    }
+    HB_CUDA(cudaMemsetAsync(b->d_ctr + CT_WORK, 0, sizeof(int), st));
+    if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[0], st));
+    HB_CUDA(launch_sweep_batch(st, b->variant, b->grid, b->d_probs, b->d_items, b->nitems, b->d_ctr));
+    if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[1], st));
+    for (int p = 0; p < P; ++p) {
+        hawkes_ctx* c = b->probs[p];
+        k_finalize<<<c->final_blocks, 256, 0, st>>>(c->acc, c->t, c->cc, c->npad, 0, c->n, 1,
+                                                    c->fixlist, c->ctr, c->partials, nullptr);
+        k_rows64<<<b->sms, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model1, c->n,
+                                         c->npad, 0, 0, 1, c->fixlist, c->ctr, c->acc, c->fix7,
+                                         nullptr);
+        k_reduce<<<1, 256, 0, st>>>(c->partials, c->final_blocks, c->fix7, c->cc, d_out + 7 * p,
+                                    c->ctr);
+    }
+    HB_CUDA(cudaGetLastError());
+    return HAWKES_OK;
+}
+
+int latched_errors(hawkes_batch* b) {
+    int err = 0;
+    HB_CUDA(cudaMemcpyAsync(&err, b->d_ctr + CT_ERR, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    for (auto* c : b->probs) {
+        int e = 0;
+        HB_CUDA(cudaMemcpyAsync(&e, c->ctr + CT_ERR, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+        HB_CUDA(cudaStreamSynchronize(b->stream));
+        if (e != 0) {
+            HB_CUDA(cudaMemsetAsync(c->ctr + CT_ERR, 0, sizeof(int), b->stream));
+            if (err == 0) err = e;
+        }
+    }
+    HB_CUDA(cudaStreamSynchronize(b->stream));
+    if (err != 0) HB_CUDA(cudaMemsetAsync(b->d_ctr + CT_ERR, 0, sizeof(int), b->stream));
+    return err;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hawkes_batch_create(hawkes_batch** out, hawkes_ctx* const* problems, int32_t n_problems,
+                        const uint64_t* seeds, const uint64_t* streams, uint32_t flags,
+                        void* cuda_stream) {
+    if (!out) return HAWKES_ERR_ARG;
+    *out = nullptr;
+    if (!problems || n_problems < 1 || (flags & ~static_cast<uint32_t>(HAWKES_MODEL1)) != 0 ||
+        (seeds == nullptr) != (streams == nullptr))
+        return HAWKES_ERR_ARG;
+    const int dev = problems[0] ? problems[0]->device : -1;
+    for (int32_t p = 0; p < n_problems; ++p) {
+        const hawkes_ctx* c = problems[p];
+        if (!c || c->device != dev) return HAWKES_ERR_ARG;
+        if (c->n == 0 || (seeds && !c->counties_ok)) return HAWKES_ERR_STATE;
+        for (int32_t q = 0; q < p; ++q)
+            if (problems[q] == c) return HAWKES_ERR_ARG;  // one context appears once
+    }
+    DeviceGuard g(dev);
+    hawkes_batch* b = new (std::nothrow) hawkes_batch();
+    if (!b) return HAWKES_ERR_OOM;
+    b->device = dev;
+    b->flags = flags;
+    b->probs.assign(problems, problems + n_problems);
+    if (seeds) {
+        b->seeds.assign(seeds, seeds + n_problems);
+        b->streams.assign(streams, streams + n_problems);
+        b->resample = true;
+    }
+    int rc = HAWKES_OK;
+    do {
+        if ((rc = st_of(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev)))) break;
+        if (cuda_stream) {
+            b->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            if ((rc = st_of(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)))) break;
+            b->own_stream = true;
+        }
+        if ((rc = st_of(cudaEventCreate(&b->ev[0]))) || (rc = st_of(cudaEventCreate(&b->ev[1])))) break;
+        if ((rc = st_of(cudaMalloc(&b->d_ctr, CT_COUNT * sizeof(int))))) break;
+        if ((rc = st_of(cudaMalloc(&b->d_iter, sizeof(uint64_t))))) break;
+        if ((rc = st_of(cudaMemsetAsync(b->d_ctr, 0, CT_COUNT * sizeof(int), b->stream)))) break;
+        if ((rc = st_of(cudaMemsetAsync(b->d_iter, 0, sizeof(uint64_t), b->stream)))) break;
+        std::vector<ProbDesc> descs;
+        for (auto* c : b->probs) descs.push_back(ProbDesc{c->rec, c->lo, c->hi, c->tb, c->cc, c->acc, c->n, c->npad});
+        if ((rc = st_of(cudaMalloc(&b->d_probs, descs.size() * sizeof(ProbDesc))))) break;
+        if ((rc = st_of(cudaMemcpyAsync(b->d_probs, descs.data(), descs.size() * sizeof(ProbDesc),
+                                        cudaMemcpyHostToDevice, b->stream))))
+            break;
+        // the contexts' own queued work must finish before the batch touches their buffers
+        for (auto* c : b->probs)
+            if ((rc = st_of(cudaStreamSynchronize(c->stream)))) break;
+        if (rc) break;
+        rc = build_items(b, 0, CHUNK, 1);
+    } while (0);
+    if (rc != HAWKES_OK) {
+        hawkes_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return HAWKES_OK;
+}
+
+void hawkes_batch_destroy(hawkes_batch* b) {
+    if (!b) return;
+    DeviceGuard g(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_probs) cudaFree(b->d_probs);
+    if (b->d_ctr) cudaFree(b->d_ctr);
+    if (b->d_iter) cudaFree(b->d_iter);
+    for (auto& e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+int hawkes_batch_run(hawkes_batch* b, const hawkes_params* d_params, uint64_t iteration,
+                     double* d_out) {
+    if (!b || !d_params || !d_out) return HAWKES_ERR_ARG;
+    DeviceGuard g(b->device);
+    k_set_u64<<<1, 32, 0, b->stream>>>(b->d_iter, iteration);
+    HB_CUDA(cudaGetLastError());
+    if (b->exec && b->g_params == d_params && b->g_out == d_out)
+        return st_of(cudaGraphLaunch(b->exec, b->stream));
+    return enqueue(b, d_params, d_out, false);
+}
+
+int hawkes_batch_capture(hawkes_batch* b, const hawkes_params* d_params, double* d_out) {
+    if (!b || !d_params || !d_out) return HAWKES_ERR_ARG;
+    DeviceGuard g(b->device);
+    HB_CUDA(cudaStreamSynchronize(b->stream));
+    drop_graph(b);
+    HB_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue(b, d_params, d_out, false);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc != HAWKES_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != HAWKES_OK ? rc : HAWKES_ERR_CUDA;
+    }
+    b->graph = graph;
+    if (cudaGraphInstantiate(&b->exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        drop_graph(b);
+        return HAWKES_ERR_CUDA;
+    }
+    b->g_params = d_params;
+    b->g_out = d_out;
+    return HAWKES_OK;
+}
+
+int hawkes_batch_wait(hawkes_batch* b) {
+    if (!b) return HAWKES_ERR_ARG;
+    DeviceGuard g(b->device);
+    HB_CUDA(cudaStreamSynchronize(b->stream));
+    return latched_errors(b);
+}
+
+int hawkes_batch_tune(hawkes_batch* b, const hawkes_params* d_params, double* d_out, int reps,
+                      int* variant, int* chunk, int* order, double* best_ms) {
+    if (!b || !d_params || !d_out || reps < 1) return HAWKES_ERR_ARG;
+    DeviceGuard g(b->device);
+    static const int kChunks[] = {16, 32, 64};
+    int bv = -1, bc = 0, bo = 0;
+    double bms = 0.0;
+    for (int v = 0; v < sweep_num_variants(); ++v) {
+        for (int o = 0; o < 2; ++o) {
+            for (int ch : kChunks) {
+                HB_TRY(build_items(b, v, ch, o));
+                HB_TRY(enqueue(b, d_params, d_out, false));  // warm-up
+                double tot = 0.0;
+                for (int r = 0; r < reps; ++r) {
+                    HB_TRY(enqueue(b, d_params, d_out, true));
+                    HB_CUDA(cudaEventSynchronize(b->ev[1]));
+                    float ms = 0.f;
+                    HB_CUDA(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+                    tot += ms;
+                }
+                const double t = tot / reps;
+                if (bv < 0 || t < bms) {
+                    bv = v;
+                    bc = ch;
+                    bo = o;
+                    bms = t;
+                }
+            }
+        }
+    }
+    HB_TRY(build_items(b, bv, bc, bo));
+    HB_CUDA(cudaStreamSynchronize(b->stream));
+    if (variant) *variant = bv;
+    if (chunk) *chunk = bc;
+    if (order) *order = bo;
+    if (best_ms) *best_ms = bms;
+    return latched_errors(b);
+}
+
+int hawkes_batch_set_config(hawkes_batch* b, int variant, int chunk, int order) {
+    if (!b || variant < 0 || variant >= sweep_num_variants() || chunk < 1 || order < 0 ||
+        order > 1)
+        return HAWKES_ERR_ARG;
+    DeviceGuard g(b->device);
+    HB_CUDA(cudaStreamSynchronize(b->stream));
+    return build_items(b, variant, chunk, order);
+}
+
+}  // extern "C"

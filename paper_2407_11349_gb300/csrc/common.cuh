@@ -59,6 +59,18 @@ __host__ __device__ __forceinline__ const float4* rec_q(const Rec* base, int64_t
 // every pair term with a padding event is exactly 0 (and finite products).
 constexpr float PAD_T = 1.0e15f;
 
+// One problem of the pair sweep: its staged records, tie ranges, time bases,
+// per-call constants and accumulators (all device pointers).
+struct ProbDesc {
+    const Rec* rec;
+    const int32_t* lo;
+    const int32_t* hi;
+    const double* tb;
+    const double* cc;
+    double* acc;
+    int64_t n, npad;
+};
+
 // Per-call constants, computed on the device from the parameters.
 enum {
     CC_KX = 0,      // sqrt(a_x)

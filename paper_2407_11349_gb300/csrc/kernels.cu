@@ -402,8 +402,9 @@ __device__ __forceinline__ double unit53(uint64_t w) {
 __global__ void k_resample(const int32_t* __restrict__ county, int64_t n,
                            const double* __restrict__ tri_xy, const double* __restrict__ cum,
                            const int32_t* __restrict__ first, const int32_t* __restrict__ last,
-                           uint64_t seed, uint64_t stream, uint64_t iteration, double* x,
-                           double* y) {
+                           uint64_t seed, uint64_t stream, uint64_t iteration,
+                           const uint64_t* d_iteration, double* x, double* y) {
+    if (d_iteration) iteration = *d_iteration;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = county[i];

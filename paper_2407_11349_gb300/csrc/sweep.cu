@@ -57,7 +57,7 @@ struct Rows {
 //   EXC    evaluate the excitation term (sources strictly earlier)
 //   COL    also accumulate the background into the source columns
 // rlo/rhi: shared-memory lo/hi of the lane's rows (masked tiles only).
-template <int RP, int MASK, bool EXC, bool COL>
+template <int RP, int UNROLL, int MASK, bool EXC, bool COL>
 __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j0, int lane,
                                           Rows<RP>& rr, float2 nomt,
                                           const int* __restrict__ rlo,
@@ -65,7 +65,7 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
 #pragma unroll 1
     for (int ch = 0; ch < TC / 32; ++ch) {
         float2 cB = f2(0.f, 0.f), cBr = f2(0.f, 0.f), cBt = f2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll UNROLL
         for (int s = 0; s < 32; ++s) {
             const int c = ch * 32 + ((lane + s) & 31);
             const float4 q0 = tile[0 * TC + c];  // -t, -t, -xh, -xh
@@ -147,18 +147,23 @@ struct Geo {
     static constexpr size_t SMEM = SMEM_TILES + SMEM_COLACC + SMEM_LOHI;
 };
 
+enum { MODE_WIN = 0, MODE_SYM = 1, MODE_BATCH = 2 };
+
 // Persistent sweep over work items.
-//   SYM: item k = items[k] = (row tile, first column tile, end column tile)
-//   window: item k -> row tile item0 + k / nch, column chunk k % nch
-template <int RP, int MINB, bool SYM>
+//   MODE_SYM:   item k = items[k] = (row tile, first column tile, end column
+//               tile) of problem `one`
+//   MODE_BATCH: as MODE_SYM, item.w = index into probs[] (many problems, one
+//               launch, one queue)
+//   MODE_WIN:   item k -> row tile item0 + k / nch, column chunk k % nch of
+//               problem `one`, rows [row_begin, row_end) only
+template <int RP, int MINB, int UNROLL, int MODE>
 __global__ void __launch_bounds__(THREADS, MINB)
-    k_sweep(const Rec* __restrict__ rec, const int32_t* __restrict__ lo,
-            const int32_t* __restrict__ hi, const double* __restrict__ tb,
-            const double* __restrict__ cc, double* __restrict__ acc, int* __restrict__ ctr,
-            const int4* __restrict__ items, int nitems, int64_t n, int64_t npad,
-            int64_t row_begin, int64_t row_end, int item0, int nch) {
+    k_sweep(ProbDesc one, const ProbDesc* __restrict__ probs, const int4* __restrict__ items,
+            int nitems, int* __restrict__ ctr, int64_t row_begin, int64_t row_end, int item0,
+            int nch) {
     using G = Geo<RP>;
     constexpr int R = G::R;
+    constexpr bool SYM = MODE != MODE_WIN;
     extern __shared__ __align__(128) unsigned char smem[];
     Rec* tiles = reinterpret_cast<Rec*>(smem);
     float* colacc = reinterpret_cast<float*>(smem + G::SMEM_TILES);
@@ -166,9 +171,14 @@ __global__ void __launch_bounds__(THREADS, MINB)
     int* shi = slo + THREADS * R;
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_item, s_abort;
+    // The current item's problem.  In batch mode it is re-read from shared
+    // memory (volatile: not kept in registers) wherever it is needed outside
+    // the pair loop, so the pair loop is compiled as in the one-problem modes.
+    __shared__ __align__(16) ProbDesc s_pd;
+    volatile ProbDesc* vpd = &s_pd;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (cc[CC_VALID] == 0.0) return;
+    if (MODE != MODE_BATCH && one.cc[CC_VALID] == 0.0) return;
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -178,33 +188,48 @@ __global__ void __launch_bounds__(THREADS, MINB)
     for (int k = tid; k < 2 * 3 * TC; k += THREADS) colacc[k] = 0.f;
     __syncthreads();
 
-    const float omt = static_cast<float>(cc[CC_OMT]);
-    const float2 nomt = f2(-omt, -omt);
-    const double kt = cc[CC_KT];
-    const double sr = cc[CC_SR], st = cc[CC_ST], set = cc[CC_SET], seq = cc[CC_SEQ];
-    const int ncol_tiles = static_cast<int>((n + TC - 1) / TC);
     uint32_t parbits = 0u;   // bit b: parity of the next phase of buffer b
     uint32_t pendbits = 0u;  // thread 0, bit b: a copy into buffer b is in flight
     int* mylo = slo + tid * R;
     int* myhi = shi + tid * R;
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(ctr + CT_WORK, 1);
+        if (tid == 0) {
+            const int k = atomicAdd(ctr + CT_WORK, 1);
+            s_item = k;
+            if (MODE == MODE_BATCH && k < nitems) {
+                const ProbDesc d = probs[items[k].w];
+                vpd->rec = d.rec; vpd->lo = d.lo; vpd->hi = d.hi; vpd->tb = d.tb;
+                vpd->cc = d.cc; vpd->acc = d.acc; vpd->n = d.n; vpd->npad = d.npad;
+            }
+        }
         __syncthreads();
         const int item = s_item;
         if (item >= nitems || s_abort) break;
         int64_t I;
         int jb, je;
+#define HK_PD(field) (MODE == MODE_BATCH ? vpd->field : one.field)
         if (SYM) {
             const int4 it = items[item];
             I = it.x;
             jb = it.y;
             je = it.z;
         } else {
+            const int ncol_tiles = static_cast<int>((one.n + TC - 1) / TC);
             I = item0 + item / nch;
             jb = (item % nch) * CHUNK;
             je = min(jb + CHUNK, ncol_tiles);
         }
+        const double* cc = HK_PD(cc);
+        if (MODE == MODE_BATCH && cc[CC_VALID] == 0.0) {  // problem with invalid parameters
+            __syncthreads();
+            continue;
+        }
+        const float omt = static_cast<float>(cc[CC_OMT]);
+        const float2 nomt = f2(-omt, -omt);
+        const double kt = cc[CC_KT];
+        const int64_t n = HK_PD(n);
+
         const int64_t r0 = I * G::TR + warp * G::WROWS;  // warp's first row
         bool live = r0 < n;
         if (!SYM) live = live && r0 < row_end && r0 + G::WROWS > row_begin;
@@ -213,6 +238,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
         float t0[R];
 #pragma unroll
         for (int p = 0; p < RP; ++p) {
+            const Rec* rec = HK_PD(rec);
+            const int32_t* plo = HK_PD(lo);
+            const int32_t* phi = HK_PD(hi);
             const int64_t i0 = r0 + lane + 64 * p, i1 = i0 + 32;
             const float4 a0 = *rec_q(rec, i0, 0), b0 = *rec_q(rec, i0, 1), c0 = *rec_q(rec, i0, 2);
             const float4 a1 = *rec_q(rec, i1, 0), b1 = *rec_q(rec, i1, 1), c1 = *rec_q(rec, i1, 2);
@@ -223,20 +251,20 @@ __global__ void __launch_bounds__(THREADS, MINB)
             rr.yh[p] = f2(-b0.z, -b1.z);
             rr.yl[p] = f2(-c0.x, -c1.x);
             rr.sB[p] = rr.sBr[p] = rr.sBt[p] = rr.sE[p] = rr.sEt[p] = rr.sEq[p] = f2(0.f, 0.f);
-            mylo[2 * p] = lo[i0];
-            mylo[2 * p + 1] = lo[i1];
-            myhi[2 * p] = hi[i0];
-            myhi[2 * p + 1] = hi[i1];
+            mylo[2 * p] = plo[i0];
+            mylo[2 * p + 1] = plo[i1];
+            myhi[2 * p] = phi[i0];
+            myhi[2 * p + 1] = phi[i1];
         }
-        const int lo_first = live ? lo[r0] : 0;
-        const int hi_last = live ? hi[min(r0 + G::WROWS, n) - 1] : 0;
-        const double trow = tb[r0 / TB];
+        const int lo_first = live ? HK_PD(lo)[r0] : 0;
+        const int hi_last = live ? HK_PD(hi)[min(r0 + G::WROWS, n) - 1] : 0;
+        const double trow = HK_PD(tb)[r0 / TB];
         const int nJ = je - jb;
 
         if (tid == 0) {
             for (int q = 0; q < 2 && q < nJ; ++q) {
                 mbar_arrive_expect_tx(&bars[q], TC * sizeof(Rec));
-                tma_load_1d(tiles + q * TC, rec + static_cast<int64_t>(jb + q) * TC,
+                tma_load_1d(tiles + q * TC, HK_PD(rec) + static_cast<int64_t>(jb + q) * TC,
                             TC * sizeof(Rec), &bars[q]);
                 pendbits |= 1u << q;
             }
@@ -253,7 +281,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
             const int jt = jb + J;
             const int j0 = jt * TC;
             if (live) {
-                const float dT = static_cast<float>((trow - tb[jt]) * kt);
+                const float dT = static_cast<float>((trow - HK_PD(tb)[jt]) * kt);
 #pragma unroll
                 for (int p = 0; p < RP; ++p) rr.tp[p] = f2(t0[2 * p] + dT, t0[2 * p + 1] + dT);
                 const float4* tile = reinterpret_cast<const float4*>(tiles + buf * TC);
@@ -261,23 +289,23 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 if (SYM) {
                     if (j0 < r0 + G::WROWS) {
                         if (j0 + TC > lo_first)
-                            tile_pass<RP, M_LOWER, true, true>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                            tile_pass<RP, UNROLL, M_LOWER, true, true>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                         else
-                            tile_pass<RP, M_NONE, true, true>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                            tile_pass<RP, UNROLL, M_NONE, true, true>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                     }
                 } else {
                     if (j0 + TC <= lo_first)
-                        tile_pass<RP, M_NONE, true, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                        tile_pass<RP, UNROLL, M_NONE, true, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                     else if (j0 >= hi_last)
-                        tile_pass<RP, M_NONE, false, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                        tile_pass<RP, UNROLL, M_NONE, false, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                     else
-                        tile_pass<RP, M_TWO, true, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                        tile_pass<RP, UNROLL, M_TWO, true, false>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
                 }
             }
             __syncthreads();
             if (tid == 0 && J + 2 < nJ && !s_abort) {
                 mbar_arrive_expect_tx(&bars[buf], TC * sizeof(Rec));
-                tma_load_1d(tiles + buf * TC, rec + static_cast<int64_t>(jt + 2) * TC,
+                tma_load_1d(tiles + buf * TC, HK_PD(rec) + static_cast<int64_t>(jt + 2) * TC,
                             TC * sizeof(Rec), &bars[buf]);
                 pendbits |= 1u << buf;
             }
@@ -286,9 +314,11 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 const float v0 = ca[tid], v1 = ca[TC + tid], v2 = ca[2 * TC + tid];
                 if (v0 != 0.f || v1 != 0.f || v2 != 0.f) {
                     const int64_t j = static_cast<int64_t>(j0) + tid;
+                    double* acc = HK_PD(acc);
+                    const int64_t npad = HK_PD(npad);
                     atomicAdd(acc + 0 * npad + j, static_cast<double>(v0));
-                    atomicAdd(acc + 1 * npad + j, static_cast<double>(v1) * sr);
-                    atomicAdd(acc + 2 * npad + j, static_cast<double>(v2) * st);
+                    atomicAdd(acc + 1 * npad + j, static_cast<double>(v1) * cc[CC_SR]);
+                    atomicAdd(acc + 2 * npad + j, static_cast<double>(v2) * cc[CC_ST]);
                     ca[tid] = 0.f;
                     ca[TC + tid] = 0.f;
                     ca[2 * TC + tid] = 0.f;
@@ -298,6 +328,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
         }
 
         if (live && !s_abort) {
+            double* acc = HK_PD(acc);
+            const int64_t npad = HK_PD(npad);
+            const double sr = cc[CC_SR], st = cc[CC_ST], set = cc[CC_SET], seq = cc[CC_SEQ];
 #pragma unroll
             for (int p = 0; p < RP; ++p) {
 #pragma unroll
@@ -325,6 +358,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
         }
         __syncthreads();
         if (s_abort) break;
+#undef HK_PD
     }
     // A wait that gave up may leave bulk copies in flight: let them land
     // (bounded) before the CTA's shared memory is released.
@@ -336,35 +370,35 @@ __global__ void __launch_bounds__(THREADS, MINB)
 // ---------------------------------------------------------------------------
 // Host side: kernel variants, their work lists, and launch.
 // ---------------------------------------------------------------------------
-using SweepFn = void (*)(const Rec*, const int32_t*, const int32_t*, const double*, const double*,
-                         double*, int*, const int4*, int, int64_t, int64_t, int64_t, int64_t, int,
+using SweepFn = void (*)(ProbDesc, const ProbDesc*, const int4*, int, int*, int64_t, int64_t, int,
                          int);
 
 struct Variant {
     int rp, minb;
-    SweepFn sym, win;
+    SweepFn win, sym, batch;
     size_t smem;
     int tr;
 };
 
-static const Variant kVariants[] = {
-    {4, 1, k_sweep<4, 1, true>, k_sweep<4, 1, false>, Geo<4>::SMEM, Geo<4>::TR},
-    {2, 2, k_sweep<2, 2, true>, k_sweep<2, 2, false>, Geo<2>::SMEM, Geo<2>::TR},
-};
+#define HK_VARIANT(RP, MINB, U)                                                        \
+    {RP, MINB, k_sweep<RP, MINB, U, MODE_WIN>, k_sweep<RP, MINB, U, MODE_SYM>,         \
+     k_sweep<RP, MINB, U, MODE_BATCH>, Geo<RP>::SMEM, Geo<RP>::TR}
+// (rows-per-lane pairs, resident CTAs per SM, unroll of the 32-step pair loop)
+static const Variant kVariants[] = {HK_VARIANT(4, 1, 8), HK_VARIANT(4, 1, 16), HK_VARIANT(4, 1, 32),
+                                    HK_VARIANT(4, 1, 4), HK_VARIANT(2, 2, 8)};
+#undef HK_VARIANT
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 int sweep_num_variants() { return kNumVariants; }
 int sweep_variant_rows(int v) { return kVariants[v].tr; }
 
 cudaError_t sweep_setup_attributes() {
-    for (const auto& v : kVariants) {
-        cudaError_t e = cudaFuncSetAttribute(v.sym, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(v.smem));
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(v.win, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(v.smem));
-        if (e != cudaSuccess) return e;
-    }
+    for (const auto& v : kVariants)
+        for (SweepFn f : {v.win, v.sym, v.batch}) {
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(v.smem));
+            if (e != cudaSuccess) return e;
+        }
     return cudaSuccess;
 }
 
@@ -376,32 +410,53 @@ int sweep_blocks_per_sm(int v) {
     return nb > 0 ? nb : 1;
 }
 
-// Symmetric work list for n events and variant v: (row tile, column tiles
-// [jb, je)) in chunks of CHUNK tiles, longest first.
-std::vector<int4> sweep_items(int64_t n, int v) {
+// Symmetric work list over problems of sizes ns[] for variant v: items
+// (row tile, column tiles [jb, je), problem) in chunks of `chunk` column
+// tiles.  order 0: all items longest first (ties: later row tiles first);
+// order 1: problem by problem, largest problem first, each problem's items
+// longest first, so that the source tiles and accumulators of the problems
+// in flight stay in L2 while the tail still ends on the smallest items.
+std::vector<int4> sweep_items_batch(const std::vector<int64_t>& ns, int v, int chunk, int order) {
     const int tr = kVariants[v].tr;
-    const int64_t nI = (n + tr - 1) / tr;
-    std::vector<int4> items;
-    for (int64_t I = 0; I < nI; ++I) {
-        const int nJ = static_cast<int>((std::min<int64_t>((I + 1) * tr, n) + TC - 1) / TC);
-        for (int jb = 0; jb < nJ; jb += CHUNK)
-            items.push_back(make_int4(static_cast<int>(I), jb, std::min(jb + CHUNK, nJ), 0));
-    }
-    std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) {
+    auto longest_first = [](const int4& a, const int4& b) {
         return (a.z - a.y) > (b.z - b.y) || ((a.z - a.y) == (b.z - b.y) && a.x > b.x);
-    });
+    };
+    std::vector<size_t> pidx(ns.size());
+    for (size_t p = 0; p < ns.size(); ++p) pidx[p] = p;
+    if (order == 1)
+        std::stable_sort(pidx.begin(), pidx.end(), [&](size_t a, size_t b) { return ns[a] > ns[b]; });
+    std::vector<int4> items;
+    for (size_t p : pidx) {
+        const int64_t n = ns[p];
+        const int64_t nI = (n + tr - 1) / tr;
+        const size_t first = items.size();
+        for (int64_t I = 0; I < nI; ++I) {
+            const int nJ = static_cast<int>((std::min<int64_t>((I + 1) * tr, n) + TC - 1) / TC);
+            for (int jb = 0; jb < nJ; jb += chunk)
+                items.push_back(make_int4(static_cast<int>(I), jb, std::min(jb + chunk, nJ),
+                                          static_cast<int>(p)));
+        }
+        if (order == 1) std::stable_sort(items.begin() + first, items.end(), longest_first);
+    }
+    if (order == 0) std::stable_sort(items.begin(), items.end(), longest_first);
     return items;
+}
+
+std::vector<int4> sweep_items(int64_t n, int v) { return sweep_items_batch({n}, v, CHUNK, 0); }
+
+static ProbDesc desc_of(const hawkes_ctx* c) {
+    return ProbDesc{c->rec, c->lo, c->hi, c->tb, c->cc, c->acc, c->n, c->npad};
 }
 
 cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end) {
     const Variant& v = kVariants[c->variant];
     const int grid_cap = c->sms * c->variant_bpsm;
+    const ProbDesc one = desc_of(c);
     if (sym) {
         const int nitems = c->nitems;
         const int grid = nitems < grid_cap ? nitems : grid_cap;
         if (grid <= 0) return cudaSuccess;
-        v.sym<<<grid, THREADS, v.smem, c->stream>>>(c->rec, c->lo, c->hi, c->tb, c->cc, c->acc,
-                                                    c->ctr, c->items, nitems, c->n, c->npad,
+        v.sym<<<grid, THREADS, v.smem, c->stream>>>(one, nullptr, c->items, nitems, c->ctr,
                                                     row_begin, row_end, 0, 0);
     } else {
         const int item0 = static_cast<int>(row_begin / v.tr);
@@ -411,10 +466,21 @@ cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row
         const int nitems = nrt * nch;
         const int grid = nitems < grid_cap ? nitems : grid_cap;
         if (grid <= 0) return cudaSuccess;
-        v.win<<<grid, THREADS, v.smem, c->stream>>>(c->rec, c->lo, c->hi, c->tb, c->cc, c->acc,
-                                                    c->ctr, nullptr, nitems, c->n, c->npad,
-                                                    row_begin, row_end, item0, nch);
+        v.win<<<grid, THREADS, v.smem, c->stream>>>(one, nullptr, nullptr, nitems, c->ctr, row_begin,
+                                                    row_end, item0, nch);
     }
+    return cudaGetLastError();
+}
+
+// One persistent launch over the items of many problems; ctr[CT_WORK] must be
+// zero when it starts.
+cudaError_t launch_sweep_batch(cudaStream_t st, int variant, int grid, const ProbDesc* probs,
+                               const int4* items, int nitems, int* ctr) {
+    const Variant& v = kVariants[variant];
+    if (grid > nitems) grid = nitems;
+    if (grid <= 0) return cudaSuccess;
+    ProbDesc none{};
+    v.batch<<<grid, THREADS, v.smem, st>>>(none, probs, items, nitems, ctr, 0, 0, 0, 0);
     return cudaGetLastError();
 }
 

@@ -67,6 +67,16 @@ _SIGS = {
                                    ctypes.POINTER(ctypes.c_int), _D]),
     "hawkes_loglik_grad_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, _VP,
                                                   ctypes.c_uint32, _VP, _VP]),
+    "hawkes_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int32,
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                           ctypes.c_uint32, _VP]),
+    "hawkes_batch_destroy": (None, [_VP]),
+    "hawkes_batch_run": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, _VP]),
+    "hawkes_batch_capture": (ctypes.c_int, [_VP, _VP, _VP]),
+    "hawkes_batch_wait": (ctypes.c_int, [_VP]),
+    "hawkes_batch_tune": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D]),
+    "hawkes_batch_set_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
 }
 
 
@@ -223,6 +233,81 @@ def hawkes_loglik_grad_noalloc(d_t, d_x, d_y, d_s, n, d_params, flags, d_out, st
                                             _VP(int(d_s) or None), int(n), _VP(int(d_params)),
                                             int(flags), _VP(int(d_out)), _VP(int(stream) or None)),
            "hawkes_loglik_grad_noalloc")
+
+
+def hawkes_batch_create(ctxs, seeds=None, streams=None, flags=HAWKES_F32, stream=0):
+    P = len(ctxs)
+    arr = (_VP * P)(*[c.value if isinstance(c, _VP) else c for c in ctxs])
+    sd = st = None
+    if seeds is not None:
+        sd = (ctypes.c_uint64 * P)(*[int(v) for v in seeds])
+        st = (ctypes.c_uint64 * P)(*[int(v) for v in streams])
+    h = _VP()
+    _check(lib().hawkes_batch_create(ctypes.byref(h), arr, P, sd, st, int(flags), _VP(int(stream) or None)),
+           "hawkes_batch_create")
+    return h
+
+
+def hawkes_batch_destroy(b):
+    lib().hawkes_batch_destroy(b)
+
+
+def hawkes_batch_run(b, d_params, iteration, d_out):
+    _check(lib().hawkes_batch_run(b, _VP(int(d_params)), int(iteration), _VP(int(d_out))), "hawkes_batch_run")
+
+
+def hawkes_batch_capture(b, d_params, d_out):
+    _check(lib().hawkes_batch_capture(b, _VP(int(d_params)), _VP(int(d_out))), "hawkes_batch_capture")
+
+
+def hawkes_batch_wait(b):
+    _check(lib().hawkes_batch_wait(b), "hawkes_batch_wait")
+
+
+def hawkes_batch_tune(b, d_params, d_out, reps=1):
+    """Returns (variant, chunk tiles, item order, mean sweep ms) of the fastest configuration."""
+    v, c, o, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().hawkes_batch_tune(b, _VP(int(d_params)), _VP(int(d_out)), int(reps), ctypes.byref(v),
+                                   ctypes.byref(c), ctypes.byref(o), ctypes.byref(ms)), "hawkes_batch_tune")
+    return v.value, c.value, o.value, ms.value
+
+
+def hawkes_batch_set_config(b, variant, chunk, order=1):
+    _check(lib().hawkes_batch_set_config(b, int(variant), int(chunk), int(order)), "hawkes_batch_set_config")
+
+
+class Batch:
+    """Many contexts evaluated in one persistent sweep launch (optionally a CUDA graph)."""
+
+    def __init__(self, hawkes_list, seeds=None, streams=None, flags=HAWKES_F32, stream=0):
+        self.members = list(hawkes_list)  # keep the contexts alive
+        self.b = hawkes_batch_create([h.ctx for h in self.members], seeds, streams, flags, stream)
+
+    def close(self):
+        if self.b:
+            hawkes_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, d_params, iteration, d_out):
+        hawkes_batch_run(self.b, d_params, iteration, d_out)
+
+    def capture(self, d_params, d_out):
+        hawkes_batch_capture(self.b, d_params, d_out)
+
+    def wait(self):
+        hawkes_batch_wait(self.b)
+
+    def tune(self, d_params, d_out, reps=1):
+        return hawkes_batch_tune(self.b, d_params, d_out, reps)
+
+    def set_config(self, variant, chunk, order=1):
+        hawkes_batch_set_config(self.b, variant, chunk, order)
 
 
 # --- convenience wrapper ---------------------------------------------------

@@ -1,0 +1,114 @@
+"""Batched evaluation (one persistent sweep launch over many problems, and its
+CUDA-graph replay) against one call per problem through the regular entry
+point, at the FP32-path tolerances of the parity tests."""
+import numpy as np
+import pytest
+
+from paper_2407_11349_gb300 import synth
+from paper_2407_11349_gb300.hawkes import Batch, Hawkes, HAWKES_F32, HawkesError
+
+pytestmark = pytest.mark.gpu
+
+TOL_LL32 = 1e-6
+TOL_G32 = 1e-5
+
+
+def _close(got, ref, rows, what):
+    scale = np.abs(rows[:, 1:7]).sum(axis=0)
+    e_ll = abs(got[0] - ref[0]) / abs(ref[0])
+    denom = np.maximum(np.abs(ref[1:]), 1e-3 * scale)
+    e_g = np.abs(got[1:] - ref[1:]) / np.where(denom > 0, denom, 1.0)
+    assert e_ll <= TOL_LL32, f"{what}: loglik rel err {e_ll:.3g}"
+    assert np.all(e_g <= TOL_G32), f"{what}: grad rel errs {e_g}"
+
+
+@pytest.fixture(scope="module")
+def problems():
+    torch = pytest.importorskip("torch")
+    base = synth.voronoi_dataset(20_000, n_cells=400, seed=31)
+    chains = [base] * 4
+    regions = synth.regional_subsets(base, [3_000, 7_100, 12_345], seed=32)
+    dss = chains + regions
+    params = synth.chain_params(len(dss), seed=33)
+    hks = [Hawkes(0).load(ds) for ds in dss]
+    seeds = [77] * len(dss)
+    streams = list(range(len(dss)))
+    yield torch, dss, params, hks, seeds, streams
+    for h in hks:
+        h.close()
+
+
+def _sequential(hks, params, seeds, streams, it):
+    out = []
+    for h, p, sd, st in zip(hks, params, seeds, streams):
+        h.resample(sd, st, it)
+        ref, rows = h.loglik_rows(p, HAWKES_F32)
+        out.append((ref, rows))
+    return out
+
+
+def test_batch_eager_and_graph_match_sequential(problems):
+    torch, dss, params, hks, seeds, streams = problems
+    P = len(dss)
+    dp = torch.tensor(params, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+    b = Batch(hks, seeds, streams, HAWKES_F32)
+    try:
+        torch.cuda.synchronize()
+        b.run(dp.data_ptr(), 3, dout.data_ptr())
+        b.wait()
+        got = dout.cpu().numpy()
+        ref = _sequential(hks, params, seeds, streams, 3)
+        for p in range(P):
+            _close(got[p], *ref[p], f"eager problem {p}")
+        b.capture(dp.data_ptr(), dout.data_ptr())
+        for it in (5, 6):
+            dout.zero_()
+            torch.cuda.synchronize()
+            b.run(dp.data_ptr(), it, dout.data_ptr())
+            b.wait()
+            got = dout.cpu().numpy()
+            ref = _sequential(hks, params, seeds, streams, it)
+            for p in range(P):
+                _close(got[p], *ref[p], f"graph iteration {it} problem {p}")
+    finally:
+        b.close()
+
+
+def test_batch_tune_then_still_correct(problems):
+    torch, dss, params, hks, seeds, streams = problems
+    P = len(dss)
+    dp = torch.tensor(params, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+    b = Batch(hks, seeds, streams, HAWKES_F32)
+    try:
+        torch.cuda.synchronize()
+        v, ch, order, ms = b.tune(dp.data_ptr(), dout.data_ptr(), reps=1)
+        assert 0 <= v < 5 and ch in (16, 32, 64) and order in (0, 1) and ms > 0
+        b.run(dp.data_ptr(), 9, dout.data_ptr())
+        b.wait()
+        got = dout.cpu().numpy()
+        ref = _sequential(hks, params, seeds, streams, 9)
+        for p in range(P):
+            _close(got[p], *ref[p], f"tuned problem {p}")
+    finally:
+        b.close()
+
+
+def test_batch_reports_invalid_problem(problems):
+    torch, dss, params, hks, seeds, streams = problems
+    P = len(dss)
+    bad = params.copy()
+    bad[2, 1] = -1.0  # tau_x < 0 for problem 2
+    dp = torch.tensor(bad, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+    b = Batch(hks, None, None, HAWKES_F32)
+    try:
+        torch.cuda.synchronize()
+        b.run(dp.data_ptr(), 0, dout.data_ptr())
+        with pytest.raises(HawkesError):
+            b.wait()
+        got = dout.cpu().numpy()
+        assert np.all(np.isnan(got[2])) and np.all(np.isfinite(np.delete(got, 2, axis=0)))
+    finally:
+        b.close()

@@ -95,7 +95,7 @@ def test_degenerate_and_other_parameters(hk, p):
     check_both(hk, small_grid(1800, seed=7), p=p, what=f"p={p}")
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_sweep_variants_agree(hk, variant):
     ds = small_grid(6000, seed=12)
     hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
