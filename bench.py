@@ -185,6 +185,75 @@ def bench_batch(ds_c3, steps, warmup):
                       "N=5,000..200,000 (sum 899,416); one persistent launch in a CUDA graph"}
 
 
+def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
+    """Min bulk ESS per second of exact HMC vs surrogate HMC, same data, same
+    adapted step size and metric.  cut=True: locations resampled every
+    iteration (the cut-posterior scheme); cut=False: locations held fixed,
+    so both samplers target p(Theta | X, t) exactly and their posterior
+    means must agree within Monte Carlo error.  The surrogate is trained on
+    the exact evaluations of the exact-HMC warmup from its last slow
+    adaptation window on."""
+    from paper_2407_11349_gb300 import diagnostics as dg
+    from paper_2407_11349_gb300 import hmc, synth
+    from paper_2407_11349_gb300.hawkes import MLP
+
+    # events with the model's space-time structure on a 40 x 40 grid of 50 km
+    # counties over 1,200 days (the posterior is then identified; see DESIGN.md)
+    ds = synth.clustered_dataset(n_events, T=1200.0, nx=40, ny=40, seed=4)
+    eta0 = np.log(synth.DEFAULT_PARAMS)
+    tgt = hmc.HawkesTarget(ds, chains, seed=4)
+    init = np.tile(eta0, (chains, 1)) + np.random.default_rng(4).normal(0, 0.01, (chains, 6))
+    ex = hmc.Sampler(tgt, hmc.Prior(eta0), init, n_leapfrog=leapfrog, seed=1, cut=cut)
+    ex.record = []
+    t0 = time.perf_counter()
+    last = ex.warmup(warmup)
+    t_warm = time.perf_counter() - t0
+    X, Y = hmc.training_set(ex.record[1 + last * (leapfrog + 1):])
+    ex.record = None
+    net = MLP(torch_device(), seed=2)
+    t0 = time.perf_counter()
+    net.set_data(X, Y)
+    loss = net.train(4000, batch=512, lr=1e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    q_start, eps, cov = ex.q.copy(), ex.eps.copy(), ex.cov.copy()
+    n0 = tgt.n_exact
+    d_ex, acc_ex, t_ex = ex.sample(draws)
+    ev_ex = tgt.n_exact - n0
+    su = hmc.Sampler(tgt, hmc.Prior(eta0), q_start, n_leapfrog=leapfrog, seed=5, cut=cut)
+    su.eps, su.iteration = eps, ex.iteration
+    su.set_cov(cov)
+    field = hmc.SurrogateField(net, chains)
+    n0 = tgt.n_exact
+    d_su, acc_su, t_su = su.sample(draws, field)
+    ev_su = tgt.n_exact - n0
+    s_ex, s_su = dg.summary(d_ex, hmc.NAMES), dg.summary(d_su, hmc.NAMES)
+    ess_ex = min(v["bulk_ess"] for v in s_ex.values())
+    ess_su = min(v["bulk_ess"] for v in s_su.values())
+    z = {k: abs(s_ex[k]["mean"] - s_su[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_su[k]["mcse"])
+         for k in hmc.NAMES}
+    net.close()
+    tgt.close()
+    return {"n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
+            "draws_per_chain": draws, "training_pairs": int(X.shape[0]), "train_loss": loss,
+            "exact": {"min_bulk_ess": ess_ex, "seconds": t_ex, "ess_per_s": ess_ex / t_ex,
+                      "accept": float(acc_ex.mean()), "exact_evals": ev_ex},
+            "surrogate": {"min_bulk_ess": ess_su, "seconds": t_su, "ess_per_s": ess_su / t_su,
+                          "ess_per_s_incl_warmup_and_training": ess_su / (t_su + t_warm + t_train),
+                          "accept": float(acc_su.mean()), "exact_evals": ev_su},
+            "speedup_ess_per_s": (ess_su / t_su) / (ess_ex / t_ex),
+            "warmup_s": t_warm, "train_s": t_train,
+            "mean_diff_in_mcse_units": {k: float(v) for k, v in z.items()},
+            "locations": "resampled every iteration (cut posterior)" if cut else "fixed",
+            "note": "exact and surrogate HMC share the adapted step size and dense metric; the surrogate "
+                    "is trained on the warmup's exact evaluations; data: clustered synthetic events on a "
+                    "40x40 grid of 50 km counties over 1,200 days"}
+
+
+def torch_device():
+    import torch
+    return torch.cuda.current_device()
+
+
 def cpu_baseline(ds, seconds=15.0):
     """The FP64 oracle on the host cores, on a bounded contiguous row window in
     the middle of the workload (every row against all N sources)."""
@@ -262,6 +331,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 30-chain batch measurement")
+    ap.add_argument("--hmc-n", type=int, default=50_000,
+                    help="events for the HMC ESS/s comparison (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--variant", type=int, default=-1,
                     help="sweep kernel variant (default: autotuned)")
@@ -392,6 +463,9 @@ def main():
         }
         if world == 1 and not args.no_batch and args.workload == "c3":
             out["batch30"] = bench_batch(ds, steps=3, warmup=1)
+        if world == 1 and args.hmc_n > 0 and args.workload == "c3":
+            out["hmc"] = {"cut_posterior": bench_hmc(args.hmc_n, cut=True),
+                          "fixed_locations": bench_hmc(args.hmc_n, cut=False)}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ds)
         print(json.dumps(out))

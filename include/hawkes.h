@@ -264,6 +264,67 @@ int hawkes_batch_tune(hawkes_batch* batch, const hawkes_params* d_params, double
 /* Select the sweep variant, chunk length and item order directly (drops a captured graph). */
 int hawkes_batch_set_config(hawkes_batch* batch, int variant, int chunk, int order);
 
+/*
+ * Surrogate network (no counterpart in the paper: the learned part layered on
+ * its method).  A 7 -> 256 -> 256 -> 7 multilayer perceptron with tanh hidden
+ * units maps (six standardised log-parameters, 1) to the standardised
+ * log-likelihood and its six log-parameter partials d ell / d log p_k.
+ * Trained on the GPU by this library's kernels (BF16 tensor-core products
+ * with FP32 accumulation for the 256 x 256 layer, FP32 elsewhere, Adam),
+ * evaluated inside HMC leapfrog trajectories; the exact kernel keeps the
+ * accept/reject step.
+ *
+ * Parameters, flattened (HAWKES_MLP_NPARAMS floats): W1[256 x 7], b1[256],
+ * W2[256 x 256], b2[256], W3[7 x 256], b3[7], row-major.
+ */
+#define HAWKES_MLP_NPARAMS 69639
+typedef struct hawkes_mlp hawkes_mlp;
+
+/* Create with Glorot-uniform weights (Philox stream `seed`) and zero biases. */
+int hawkes_mlp_create(hawkes_mlp** out, int device, void* cuda_stream, uint64_t seed);
+void hawkes_mlp_destroy(hawkes_mlp* mlp);
+int hawkes_mlp_get_params(hawkes_mlp* mlp, float* params);        /* host [NPARAMS], synchronous */
+int hawkes_mlp_set_params(hawkes_mlp* mlp, const float* params);  /* also resets the Adam state */
+
+/*
+ * Training set: X[n x 6] log-parameters and Y[n x 7] (log-likelihood, six
+ * log-parameter partials), host arrays, n >= 2.  Column means and standard
+ * deviations are computed on the device; inputs and targets are standardised
+ * with them (and predictions are mapped back).
+ */
+int hawkes_mlp_set_data(hawkes_mlp* mlp, int64_t n, const double* X, const double* Y);
+
+/*
+ * `steps` Adam steps (learning rate lr, betas 0.9 / 0.999) on minibatches of
+ * `batch` rows (a multiple of 64, at most 4096) drawn with replacement by a
+ * Philox stream keyed by `seed` and the step count.  *last_loss (optional)
+ * receives the last minibatch's mean squared error (standardised units).
+ */
+int hawkes_mlp_train(hawkes_mlp* mlp, int64_t steps, int batch, double lr, uint64_t seed,
+                     double* last_loss);
+
+/*
+ * One forward and backward pass without an update, for testing: host inputs
+ * Xs[batch x 7] and targets Ts[batch x 7] in standardised units; outputs the
+ * loss, the gradient grad[NPARAMS] and the network outputs Y[batch x 7]
+ * (optional pointers).
+ */
+int hawkes_mlp_loss_grad(hawkes_mlp* mlp, int batch, const float* Xs, const float* Ts,
+                         double* loss, float* grad, float* Y);
+
+/*
+ * Predictions for `count` (1..4096) parameter vectors: d_logp[count x 6]
+ * device log-parameters -> d_out[count x 7] device (log-likelihood, six
+ * log-parameter partials), queued on the network's stream.
+ */
+int hawkes_mlp_predict(hawkes_mlp* mlp, int64_t count, const double* d_logp, double* d_out);
+
+/* Standardisation statistics: mean_in[6], sd_in[6], mean_out[7], sd_out[7] (host, 26 doubles). */
+int hawkes_mlp_stats(hawkes_mlp* mlp, double* stats26);
+
+/* Wait for the network's queued work. */
+int hawkes_mlp_wait(hawkes_mlp* mlp);
+
 /* Number of events n of the current set (0 if none). */
 int64_t hawkes_num_events(const hawkes_ctx* ctx);
 

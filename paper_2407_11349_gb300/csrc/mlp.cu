@@ -1,0 +1,619 @@
+// Surrogate network of the log-likelihood and its gradient: a 7 -> 256 -> 256
+// -> 7 multilayer perceptron (tanh hidden units), trained on the GPU with
+// these kernels and evaluated inside HMC leapfrog trajectories.  The paper has
+// no surrogate: this is the learned part layered on its method.
+//
+// Inputs are the six standardised log-parameters and a constant 1; outputs
+// are the standardised log-likelihood and its six log-parameter partials.
+// Weights are kept in FP32 (Adam state and master copy); the 256 x 256 layer
+// runs on the tensor cores from BF16 copies of W2 and W2^T with BF16
+// activations and FP32 accumulation (mma.sync m16n8k16); the 7-wide layers
+// run in FP32.
+//   forward:  h1 = tanh(x W1^T + b1), h2 = tanh(h1 W2^T + b2), y = h2 W3^T + b3
+//   loss:     mean over the batch and the 7 outputs of (y - t)^2
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int DIN = 7, DH = 256, DOUT = 7;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + DH * DIN, OFF_W2 = OFF_B1 + DH, OFF_B2 = OFF_W2 + DH * DH,
+              OFF_W3 = OFF_B2 + DH, OFF_B3 = OFF_W3 + DOUT * DH, NPARAMS = OFF_B3 + DOUT;
+static_assert(NPARAMS == HAWKES_MLP_NPARAMS, "parameter count");
+constexpr int BMAX = 4096;  // largest batch (a multiple of 64)
+
+// ---------------------------------------------------------------------------
+// Tensor-core GEMM: C[M x N] = A[M x K] . Bt[N x K]^T, BF16 in, FP32 accumulate.
+// A and Bt row-major; M, N multiples of 64, K a multiple of 16.  CTA tile
+// 64 x 64 (4 warps of 32 x 32, each 2 x 4 mma tiles of 16 x 8).
+// ---------------------------------------------------------------------------
+enum { EPI_FWD2 = 0, EPI_STORE = 1, EPI_BWD1 = 2 };
+
+struct Epi {
+    const float* bias;  // EPI_FWD2: b2[N]
+    const float* h;     // EPI_BWD1: h1 (FP32, [M x N]) for the tanh derivative
+    float* out;         // [M x N] FP32
+};
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm(const bf16* __restrict__ A, int lda,
+                                              const bf16* __restrict__ Bt, int ldb, int K, Epi e,
+                                              int ldc) {
+    __shared__ __align__(16) bf16 sA[64][24];
+    __shared__ __align__(16) bf16 sB[64][24];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, t = lane & 3;
+    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+    const int lr = tid >> 1, lc = (tid & 1) * 8;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        *reinterpret_cast<uint4*>(&sA[lr][lc]) =
+            *reinterpret_cast<const uint4*>(A + static_cast<size_t>(m0 + lr) * lda + k0 + lc);
+        *reinterpret_cast<uint4*>(&sB[lr][lc]) =
+            *reinterpret_cast<const uint4*>(Bt + static_cast<size_t>(n0 + lr) * ldb + k0 + lc);
+        __syncthreads();
+        uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int rb = wm * 32 + i * 16;
+            af[i][0] = *reinterpret_cast<const uint32_t*>(&sA[rb + g][t * 2]);
+            af[i][1] = *reinterpret_cast<const uint32_t*>(&sA[rb + g + 8][t * 2]);
+            af[i][2] = *reinterpret_cast<const uint32_t*>(&sA[rb + g][t * 2 + 8]);
+            af[i][3] = *reinterpret_cast<const uint32_t*>(&sA[rb + g + 8][t * 2 + 8]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int nb = wn * 32 + j * 8;
+            bfr[j][0] = *reinterpret_cast<const uint32_t*>(&sB[nb + g][t * 2]);
+            bfr[j][1] = *reinterpret_cast<const uint32_t*>(&sB[nb + g][t * 2 + 8]);
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int m = m0 + wm * 32 + i * 16 + g + (q >= 2 ? 8 : 0);
+                const int n = n0 + wn * 32 + j * 8 + t * 2 + (q & 1);
+                const size_t o = static_cast<size_t>(m) * ldc + n;
+                float v = acc[i][j][q];
+                if (EPI == EPI_FWD2) v = tanhf(v + e.bias[n]);
+                if (EPI == EPI_BWD1) {
+                    const float h = e.h[o];
+                    v = v * (1.f - h * h);
+                }
+                e.out[o] = v;
+            }
+}
+
+// ---------------------------------------------------------------------------
+// Small layers and reductions (FP32).
+// ---------------------------------------------------------------------------
+// h1 = tanh(x W1^T + b1): FP32 copy, BF16 row-major copy, BF16 transposed copy.
+__global__ void k_l1(const float* __restrict__ X, const float* __restrict__ P, int B,
+                     float* __restrict__ H1f, bf16* __restrict__ H1b, bf16* __restrict__ H1Tb) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * DH) return;
+    const int b = idx / DH, j = idx % DH;
+    float z = P[OFF_B1 + j];
+#pragma unroll
+    for (int k = 0; k < DIN; ++k) z = fmaf(P[OFF_W1 + j * DIN + k], X[b * DIN + k], z);
+    const float h = tanhf(z);
+    H1f[idx] = h;
+    H1b[idx] = __float2bfloat16_rn(h);
+    H1Tb[static_cast<size_t>(j) * B + b] = __float2bfloat16_rn(h);
+}
+
+// y = h2 W3^T + b3; with targets: dy = 2 (y - t) / (7 B) and the loss sum.
+__global__ void k_l3(const float* __restrict__ H2f, const float* __restrict__ P, int B,
+                     const float* __restrict__ T, float* __restrict__ Y, float* __restrict__ dY,
+                     double* loss) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * DOUT) return;
+    const int b = idx / DOUT, o = idx % DOUT;
+    float y = P[OFF_B3 + o];
+    for (int j = 0; j < DH; ++j) y = fmaf(P[OFF_W3 + o * DH + j], H2f[b * DH + j], y);
+    Y[idx] = y;
+    if (T) {
+        const float d = y - T[idx];
+        dY[idx] = 2.f * d / static_cast<float>(DOUT * B);
+        atomicAdd(loss, static_cast<double>(d) * d / (DOUT * B));
+    }
+}
+
+// dz2 = (dy W3) * (1 - h2^2): FP32, BF16 row-major and BF16 transposed copies.
+__global__ void k_bwd2(const float* __restrict__ dY, const float* __restrict__ H2f,
+                       const float* __restrict__ P, int B, float* __restrict__ dZ2f,
+                       bf16* __restrict__ dZ2b, bf16* __restrict__ dZ2Tb) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= B * DH) return;
+    const int b = idx / DH, j = idx % DH;
+    float s = 0.f;
+#pragma unroll
+    for (int o = 0; o < DOUT; ++o) s = fmaf(dY[b * DOUT + o], P[OFF_W3 + o * DH + j], s);
+    const float h = H2f[idx];
+    const float d = s * (1.f - h * h);
+    dZ2f[idx] = d;
+    dZ2b[idx] = __float2bfloat16_rn(d);
+    dZ2Tb[static_cast<size_t>(j) * B + b] = __float2bfloat16_rn(d);
+}
+
+// Gradients reduced over the batch: W3, b3, b2 (after k_bwd2) or W1, b1 (after
+// the backward GEMM).  One block of 256 threads per output element.
+__global__ void k_grad_small(const float* __restrict__ dY, const float* __restrict__ H2f,
+                             const float* __restrict__ dZ2f, const float* __restrict__ dZ1f,
+                             const float* __restrict__ X, int B, int which, float* __restrict__ G) {
+    const int e = blockIdx.x;
+    float s = 0.f;
+    int dst;
+    if (which == 0) {  // W3 [7 x 256], b3 [7], b2 [256]
+        if (e < DOUT * DH) {
+            const int o = e / DH, j = e % DH;
+            for (int b = threadIdx.x; b < B; b += blockDim.x) s += dY[b * DOUT + o] * H2f[b * DH + j];
+            dst = OFF_W3 + e;
+        } else if (e < DOUT * DH + DOUT) {
+            const int o = e - DOUT * DH;
+            for (int b = threadIdx.x; b < B; b += blockDim.x) s += dY[b * DOUT + o];
+            dst = OFF_B3 + o;
+        } else {
+            const int j = e - DOUT * DH - DOUT;
+            for (int b = threadIdx.x; b < B; b += blockDim.x) s += dZ2f[b * DH + j];
+            dst = OFF_B2 + j;
+        }
+    } else {  // W1 [256 x 7], b1 [256]
+        if (e < DH * DIN) {
+            const int j = e / DIN, k = e % DIN;
+            for (int b = threadIdx.x; b < B; b += blockDim.x) s += dZ1f[b * DH + j] * X[b * DIN + k];
+            dst = OFF_W1 + e;
+        } else {
+            const int j = e - DH * DIN;
+            for (int b = threadIdx.x; b < B; b += blockDim.x) s += dZ1f[b * DH + j];
+            dst = OFF_B1 + j;
+        }
+    }
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) G[dst] = red[0];
+}
+
+// Adam step (bias-corrected, step count read from device memory) and refresh
+// of the BF16 copies of W2 and W2^T.
+__global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
+                       float* __restrict__ V, const int64_t* step, float lr, bf16* __restrict__ W2b,
+                       bf16* __restrict__ W2Tb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPARAMS) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float tt = static_cast<float>(*step + 1);  // this update's 1-based step number
+    const float g = G[i];
+    const float m = b1 * M[i] + (1.f - b1) * g;
+    const float v = b2 * V[i] + (1.f - b2) * g * g;
+    M[i] = m;
+    V[i] = v;
+    const float mh = m / (1.f - powf(b1, tt)), vh = v / (1.f - powf(b2, tt));
+    const float p = P[i] - lr * mh / (sqrtf(vh) + eps);
+    P[i] = p;
+    if (i >= OFF_W2 && i < OFF_B2) {
+        const int r = (i - OFF_W2) / DH, c = (i - OFF_W2) % DH;
+        W2b[r * DH + c] = __float2bfloat16_rn(p);
+        W2Tb[c * DH + r] = __float2bfloat16_rn(p);
+    }
+}
+
+__global__ void k_refresh_w2(const float* __restrict__ P, bf16* __restrict__ W2b,
+                             bf16* __restrict__ W2Tb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= DH * DH) return;
+    const int r = i / DH, c = i % DH;
+    const bf16 v = __float2bfloat16_rn(P[OFF_W2 + i]);
+    W2b[r * DH + c] = v;
+    W2Tb[c * DH + r] = v;
+}
+
+// Philox4x32-10 (Salmon et al. 2011) for minibatch draws and initialisation.
+__device__ __forceinline__ uint4 philox4x32(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Minibatch of B rows drawn with replacement from the n standardised rows
+// (Philox counter: row slot, completed step count); clears the loss.
+__global__ void k_gather(const float* __restrict__ Xs, const float* __restrict__ Ts, int64_t n,
+                         int B, uint64_t seed, const int64_t* step, float* __restrict__ X,
+                         float* __restrict__ T, double* loss) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t s = *step;
+    if (b < B) {
+        const uint4 r = philox4x32(make_uint4(static_cast<uint32_t>(b), static_cast<uint32_t>(s),
+                                              static_cast<uint32_t>(s >> 32), 0x4d4c50u),
+                                   make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)));
+        const uint64_t u = (static_cast<uint64_t>(r.x) << 32) | r.y;
+        const int64_t row = static_cast<int64_t>(u % static_cast<uint64_t>(n));
+        for (int k = 0; k < DIN; ++k) X[b * DIN + k] = Xs[row * DIN + k];
+        for (int k = 0; k < DOUT; ++k) T[b * DOUT + k] = Ts[row * DOUT + k];
+    }
+    if (b == 0) *loss = 0.0;
+}
+
+__global__ void k_step_done(int64_t* step) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
+}
+
+// Column means and standard deviations (FP64) of X[n x 6] and Y[n x 7], then
+// the standardised FP32 copies (the 7th input is the constant 1).
+__global__ void k_stats(const double* __restrict__ X, const double* __restrict__ Y, int64_t n,
+                        double* stats /* mean_in[6] sd_in[6] mean_out[7] sd_out[7] */) {
+    const int col = blockIdx.x;  // 0..5 inputs, 6..12 outputs
+    const double* src = col < 6 ? X : Y;
+    const int w = col < 6 ? 6 : 7, c = col < 6 ? col : col - 6;
+    double s = 0.0, s2 = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = src[i * w + c];
+        s += v;
+        s2 += v * v;
+    }
+    __shared__ double r1[256], r2[256];
+    r1[threadIdx.x] = s;
+    r2[threadIdx.x] = s2;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            r1[threadIdx.x] += r1[threadIdx.x + k];
+            r2[threadIdx.x] += r2[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mean = r1[0] / n;
+        double var = r2[0] / n - mean * mean;
+        double sd = var > 0.0 ? sqrt(var) : 0.0;
+        if (!(sd > 1e-12 * (fabs(mean) + 1e-300))) sd = 1.0;  // constant column
+        if (col < 6) {
+            stats[col] = mean;
+            stats[6 + col] = sd;
+        } else {
+            stats[12 + c] = mean;
+            stats[19 + c] = sd;
+        }
+    }
+}
+
+__global__ void k_standardise(const double* __restrict__ X, const double* __restrict__ Y, int64_t n,
+                              const double* __restrict__ st, float* __restrict__ Xs,
+                              float* __restrict__ Ts) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = 0; k < 6; ++k) Xs[i * DIN + k] = static_cast<float>((X[i * 6 + k] - st[k]) / st[6 + k]);
+        Xs[i * DIN + 6] = 1.f;
+        if (Y)
+            for (int k = 0; k < 7; ++k)
+                Ts[i * DOUT + k] = static_cast<float>((Y[i * 7 + k] - st[12 + k]) / st[19 + k]);
+    }
+}
+
+// Prediction: standardise the queries (zero-padded to B rows), and map the
+// network's outputs back to the log-likelihood and log-parameter partials.
+__global__ void k_predict_in(const double* __restrict__ q, int64_t m, int B, const double* __restrict__ st,
+                             float* __restrict__ X) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    for (int k = 0; k < 6; ++k) X[i * DIN + k] = i < m ? static_cast<float>((q[i * 6 + k] - st[k]) / st[6 + k]) : 0.f;
+    X[i * DIN + 6] = 1.f;
+}
+
+__global__ void k_predict_out(const float* __restrict__ Y, int64_t m, const double* __restrict__ st,
+                              double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m * DOUT) return;
+    const int k = i % DOUT;
+    out[i] = st[12 + k] + st[19 + k] * static_cast<double>(Y[i]);
+}
+
+__global__ void k_init_params(float* P, uint64_t seed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPARAMS) return;
+    float lim = 0.f;  // biases start at zero
+    if (i < OFF_B1) lim = sqrtf(6.f / (DH + DIN));
+    else if (i >= OFF_W2 && i < OFF_B2) lim = sqrtf(6.f / (DH + DH));
+    else if (i >= OFF_W3 && i < OFF_B3) lim = sqrtf(6.f / (DOUT + DH));
+    const uint4 r = philox4x32(make_uint4(static_cast<uint32_t>(i), 0u, 0u, 0x494e4954u),
+                               make_uint2(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32)));
+    const float u = (r.x >> 8) * (1.f / 16777216.f);
+    P[i] = lim * (2.f * u - 1.f);
+}
+
+}  // namespace
+
+struct hawkes_mlp {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+    bf16 *W2b = nullptr, *W2Tb = nullptr;
+    int64_t* step = nullptr;
+    double* loss = nullptr;
+    double* stats = nullptr;  // 26 values
+    bool have_stats = false;
+    int64_t n = 0;
+    float *Xs = nullptr, *Ts = nullptr;  // standardised data set
+    // batch work buffers (BMAX rows)
+    float *X = nullptr, *T = nullptr, *H1f = nullptr, *H2f = nullptr, *Y = nullptr, *dY = nullptr,
+          *dZ2f = nullptr, *dZ1f = nullptr;
+    bf16 *H1b = nullptr, *H1Tb = nullptr, *dZ2b = nullptr, *dZ2Tb = nullptr;
+    double* hbuf = nullptr;  // pinned host scratch
+};
+
+namespace {
+
+int st_of(cudaError_t e) {
+    if (e == cudaSuccess) return HAWKES_OK;
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? HAWKES_ERR_OOM : HAWKES_ERR_CUDA;
+}
+#define HM_TRY(expr)                      \
+    do {                                  \
+        int _rc = (expr);                 \
+        if (_rc != HAWKES_OK) return _rc; \
+    } while (0)
+#define HM_CUDA(expr) HM_TRY(st_of(expr))
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+int alloc(T** p, size_t count) {
+    return st_of(cudaMalloc(reinterpret_cast<void**>(p), (count ? count : 1) * sizeof(T)));
+}
+
+// Forward (and, with targets, backward) of a batch already in m->X (and m->T).
+int forward_backward(hawkes_mlp* m, int B, bool train) {
+    cudaStream_t st = m->stream;
+    const int gH = (B * DH + 255) / 256, gO = (B * DOUT + 255) / 256;
+    k_l1<<<gH, 256, 0, st>>>(m->X, m->P, B, m->H1f, m->H1b, m->H1Tb);
+    Epi e2{m->P + OFF_B2, nullptr, m->H2f};
+    k_gemm<EPI_FWD2><<<dim3(DH / 64, B / 64), 128, 0, st>>>(m->H1b, DH, m->W2b, DH, DH, e2, DH);
+    k_l3<<<gO, 256, 0, st>>>(m->H2f, m->P, B, train ? m->T : nullptr, m->Y, m->dY, m->loss);
+    if (train) {
+        k_bwd2<<<gH, 256, 0, st>>>(m->dY, m->H2f, m->P, B, m->dZ2f, m->dZ2b, m->dZ2Tb);
+        k_grad_small<<<DOUT * DH + DOUT + DH, 256, 0, st>>>(m->dY, m->H2f, m->dZ2f, nullptr, m->X, B,
+                                                            0, m->G);
+        Epi ew{nullptr, nullptr, m->G + OFF_W2};
+        k_gemm<EPI_STORE><<<dim3(DH / 64, DH / 64), 128, 0, st>>>(m->dZ2Tb, B, m->H1Tb, B, B, ew, DH);
+        Epi eb{nullptr, m->H1f, m->dZ1f};
+        k_gemm<EPI_BWD1><<<dim3(DH / 64, B / 64), 128, 0, st>>>(m->dZ2b, DH, m->W2Tb, DH, DH, eb, DH);
+        k_grad_small<<<DH * DIN + DH, 256, 0, st>>>(nullptr, nullptr, nullptr, m->dZ1f, m->X, B, 1, m->G);
+    }
+    return st_of(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+int hawkes_mlp_create(hawkes_mlp** out, int device, void* cuda_stream, uint64_t seed) {
+    if (!out) return HAWKES_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return device < 0 ? HAWKES_ERR_ARG : HAWKES_ERR_CUDA;
+    }
+    DeviceGuard g(device);
+    hawkes_mlp* m = new (std::nothrow) hawkes_mlp();
+    if (!m) return HAWKES_ERR_OOM;
+    m->device = device;
+    int rc = HAWKES_OK;
+    do {
+        if (cuda_stream) {
+            m->stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            if ((rc = st_of(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking)))) break;
+            m->own_stream = true;
+        }
+        if ((rc = alloc(&m->P, NPARAMS)) || (rc = alloc(&m->G, NPARAMS)) || (rc = alloc(&m->M, NPARAMS)) ||
+            (rc = alloc(&m->V, NPARAMS)) || (rc = alloc(&m->W2b, DH * DH)) || (rc = alloc(&m->W2Tb, DH * DH)) ||
+            (rc = alloc(&m->step, 1)) || (rc = alloc(&m->loss, 1)) || (rc = alloc(&m->stats, 26)) ||
+            (rc = alloc(&m->X, BMAX * DIN)) || (rc = alloc(&m->T, BMAX * DOUT)) ||
+            (rc = alloc(&m->H1f, BMAX * DH)) || (rc = alloc(&m->H2f, BMAX * DH)) ||
+            (rc = alloc(&m->Y, BMAX * DOUT)) || (rc = alloc(&m->dY, BMAX * DOUT)) ||
+            (rc = alloc(&m->dZ2f, BMAX * DH)) || (rc = alloc(&m->dZ1f, BMAX * DH)) ||
+            (rc = alloc(&m->H1b, BMAX * DH)) || (rc = alloc(&m->H1Tb, BMAX * DH)) ||
+            (rc = alloc(&m->dZ2b, BMAX * DH)) || (rc = alloc(&m->dZ2Tb, BMAX * DH)))
+            break;
+        if ((rc = st_of(cudaMallocHost(reinterpret_cast<void**>(&m->hbuf), 64 * sizeof(double))))) break;
+        k_init_params<<<(NPARAMS + 255) / 256, 256, 0, m->stream>>>(m->P, seed);
+        k_refresh_w2<<<DH * DH / 256, 256, 0, m->stream>>>(m->P, m->W2b, m->W2Tb);
+        if ((rc = st_of(cudaMemsetAsync(m->M, 0, NPARAMS * sizeof(float), m->stream))) ||
+            (rc = st_of(cudaMemsetAsync(m->V, 0, NPARAMS * sizeof(float), m->stream))) ||
+            (rc = st_of(cudaMemsetAsync(m->step, 0, sizeof(int64_t), m->stream))) ||
+            (rc = st_of(cudaStreamSynchronize(m->stream))))
+            break;
+    } while (0);
+    if (rc != HAWKES_OK) {
+        hawkes_mlp_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return HAWKES_OK;
+}
+
+void hawkes_mlp_destroy(hawkes_mlp* m) {
+    if (!m) return;
+    DeviceGuard g(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    for (void* p : {(void*)m->P, (void*)m->G, (void*)m->M, (void*)m->V, (void*)m->W2b, (void*)m->W2Tb,
+                    (void*)m->step, (void*)m->loss, (void*)m->stats, (void*)m->Xs, (void*)m->Ts,
+                    (void*)m->X, (void*)m->T, (void*)m->H1f, (void*)m->H2f, (void*)m->Y, (void*)m->dY,
+                    (void*)m->dZ2f, (void*)m->dZ1f, (void*)m->H1b, (void*)m->H1Tb, (void*)m->dZ2b,
+                    (void*)m->dZ2Tb})
+        if (p) cudaFree(p);
+    if (m->hbuf) cudaFreeHost(m->hbuf);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    cudaGetLastError();
+    delete m;
+}
+
+int hawkes_mlp_get_params(hawkes_mlp* m, float* params) {
+    if (!m || !params) return HAWKES_ERR_ARG;
+    DeviceGuard g(m->device);
+    HM_CUDA(cudaMemcpyAsync(params, m->P, NPARAMS * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    return st_of(cudaStreamSynchronize(m->stream));
+}
+
+int hawkes_mlp_set_params(hawkes_mlp* m, const float* params) {
+    if (!m || !params) return HAWKES_ERR_ARG;
+    DeviceGuard g(m->device);
+    HM_CUDA(cudaMemcpyAsync(m->P, params, NPARAMS * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    k_refresh_w2<<<DH * DH / 256, 256, 0, m->stream>>>(m->P, m->W2b, m->W2Tb);
+    HM_CUDA(cudaMemsetAsync(m->M, 0, NPARAMS * sizeof(float), m->stream));
+    HM_CUDA(cudaMemsetAsync(m->V, 0, NPARAMS * sizeof(float), m->stream));
+    HM_CUDA(cudaMemsetAsync(m->step, 0, sizeof(int64_t), m->stream));
+    return st_of(cudaStreamSynchronize(m->stream));
+}
+
+int hawkes_mlp_set_data(hawkes_mlp* m, int64_t n, const double* X, const double* Y) {
+    if (!m || n < 2 || !X || !Y) return HAWKES_ERR_ARG;
+    DeviceGuard g(m->device);
+    HM_CUDA(cudaStreamSynchronize(m->stream));
+    if (m->Xs) cudaFree(m->Xs);
+    if (m->Ts) cudaFree(m->Ts);
+    m->Xs = m->Ts = nullptr;
+    double *dX = nullptr, *dY = nullptr;
+    int rc = HAWKES_OK;
+    if ((rc = alloc(&m->Xs, n * DIN)) || (rc = alloc(&m->Ts, n * DOUT)) || (rc = alloc(&dX, n * 6)) ||
+        (rc = alloc(&dY, n * 7))) {
+        if (dX) cudaFree(dX);
+        if (dY) cudaFree(dY);
+        return rc;
+    }
+    cudaStream_t st = m->stream;
+    if ((rc = st_of(cudaMemcpyAsync(dX, X, n * 6 * sizeof(double), cudaMemcpyHostToDevice, st))) == HAWKES_OK &&
+        (rc = st_of(cudaMemcpyAsync(dY, Y, n * 7 * sizeof(double), cudaMemcpyHostToDevice, st))) == HAWKES_OK) {
+        k_stats<<<13, 256, 0, st>>>(dX, dY, n, m->stats);
+        k_standardise<<<256, 256, 0, st>>>(dX, dY, n, m->stats, m->Xs, m->Ts);
+        rc = st_of(cudaStreamSynchronize(st));
+    }
+    cudaFree(dX);
+    cudaFree(dY);
+    if (rc != HAWKES_OK) return rc;
+    m->n = n;
+    m->have_stats = true;
+    return HAWKES_OK;
+}
+
+int hawkes_mlp_train(hawkes_mlp* m, int64_t steps, int batch, double lr, uint64_t seed,
+                     double* last_loss) {
+    if (!m || steps < 0 || batch < 64 || batch > BMAX || batch % 64 != 0 || !(lr > 0)) return HAWKES_ERR_ARG;
+    if (!m->have_stats || !m->Xs) return HAWKES_ERR_STATE;
+    DeviceGuard g(m->device);
+    for (int64_t s = 0; s < steps; ++s) {
+        k_gather<<<(batch + 255) / 256, 256, 0, m->stream>>>(m->Xs, m->Ts, m->n, batch, seed, m->step,
+                                                            m->X, m->T, m->loss);
+        HM_TRY(forward_backward(m, batch, true));
+        k_adam<<<(NPARAMS + 255) / 256, 256, 0, m->stream>>>(m->P, m->G, m->M, m->V, m->step,
+                                                             static_cast<float>(lr), m->W2b, m->W2Tb);
+        k_step_done<<<1, 32, 0, m->stream>>>(m->step);
+    }
+    HM_CUDA(cudaGetLastError());
+    if (last_loss) {
+        HM_CUDA(cudaMemcpyAsync(m->hbuf, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+        HM_CUDA(cudaStreamSynchronize(m->stream));
+        *last_loss = m->hbuf[0];
+    }
+    return HAWKES_OK;
+}
+
+int hawkes_mlp_loss_grad(hawkes_mlp* m, int batch, const float* Xs, const float* Ts, double* loss,
+                         float* grad, float* Y) {
+    if (!m || batch < 64 || batch > BMAX || batch % 64 != 0 || !Xs || !Ts) return HAWKES_ERR_ARG;
+    DeviceGuard g(m->device);
+    cudaStream_t st = m->stream;
+    HM_CUDA(cudaMemcpyAsync(m->X, Xs, batch * DIN * sizeof(float), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemcpyAsync(m->T, Ts, batch * DOUT * sizeof(float), cudaMemcpyHostToDevice, st));
+    HM_CUDA(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
+    HM_TRY(forward_backward(m, batch, true));
+    if (grad) HM_CUDA(cudaMemcpyAsync(grad, m->G, NPARAMS * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (Y) HM_CUDA(cudaMemcpyAsync(Y, m->Y, batch * DOUT * sizeof(float), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaMemcpyAsync(m->hbuf, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (loss) *loss = m->hbuf[0];
+    return HAWKES_OK;
+}
+
+int hawkes_mlp_predict(hawkes_mlp* m, int64_t count, const double* d_logp, double* d_out) {
+    if (!m || count < 1 || count > BMAX || !d_logp || !d_out) return HAWKES_ERR_ARG;
+    if (!m->have_stats) return HAWKES_ERR_STATE;
+    DeviceGuard g(m->device);
+    const int B = static_cast<int>((count + 63) / 64 * 64);
+    k_predict_in<<<(B + 255) / 256, 256, 0, m->stream>>>(d_logp, count, B, m->stats, m->X);
+    HM_TRY(forward_backward(m, B, false));
+    k_predict_out<<<static_cast<int>((count * DOUT + 255) / 256), 256, 0, m->stream>>>(m->Y, count, m->stats,
+                                                                                     d_out);
+    return st_of(cudaGetLastError());
+}
+
+int hawkes_mlp_stats(hawkes_mlp* m, double* stats26) {
+    if (!m || !stats26) return HAWKES_ERR_ARG;
+    if (!m->have_stats) return HAWKES_ERR_STATE;
+    DeviceGuard g(m->device);
+    HM_CUDA(cudaMemcpyAsync(stats26, m->stats, 26 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    return st_of(cudaStreamSynchronize(m->stream));
+}
+
+int hawkes_mlp_wait(hawkes_mlp* m) {
+    if (!m) return HAWKES_ERR_ARG;
+    DeviceGuard g(m->device);
+    return st_of(cudaStreamSynchronize(m->stream));
+}
+
+}  // extern "C"

@@ -77,6 +77,18 @@ _SIGS = {
     "hawkes_batch_tune": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D]),
     "hawkes_batch_set_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "hawkes_mlp_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_uint64]),
+    "hawkes_mlp_destroy": (None, [_VP]),
+    "hawkes_mlp_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "hawkes_mlp_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "hawkes_mlp_set_data": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
+    "hawkes_mlp_train": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _D]),
+    "hawkes_mlp_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                            ctypes.POINTER(ctypes.c_float), _D, ctypes.POINTER(ctypes.c_float),
+                                            ctypes.POINTER(ctypes.c_float)]),
+    "hawkes_mlp_predict": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP]),
+    "hawkes_mlp_stats": (ctypes.c_int, [_VP, _D]),
+    "hawkes_mlp_wait": (ctypes.c_int, [_VP]),
 }
 
 
@@ -308,6 +320,79 @@ class Batch:
 
     def set_config(self, variant, chunk, order=1):
         hawkes_batch_set_config(self.b, variant, chunk, order)
+
+
+HAWKES_MLP_NPARAMS = 69639
+_F = ctypes.POINTER(ctypes.c_float)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class MLP:
+    """The surrogate network (include/hawkes.h, hawkes_mlp_*)."""
+
+    def __init__(self, device=0, stream=0, seed=0):
+        h = _VP()
+        _check(lib().hawkes_mlp_create(ctypes.byref(h), int(device), _VP(int(stream) or None), int(seed)),
+               "hawkes_mlp_create")
+        self.m = h
+
+    def close(self):
+        if self.m:
+            lib().hawkes_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = np.zeros(HAWKES_MLP_NPARAMS, dtype=np.float32)
+        _check(lib().hawkes_mlp_get_params(self.m, p.ctypes.data_as(_F)), "hawkes_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = _f32(p)
+        _check(lib().hawkes_mlp_set_params(self.m, p.ctypes.data_as(_F)), "hawkes_mlp_set_params")
+
+    def set_data(self, X, Y):
+        X = _f64(X).reshape(-1, 6)
+        Y = _f64(Y).reshape(-1, 7)
+        _check(lib().hawkes_mlp_set_data(self.m, X.shape[0], _dp(X), _dp(Y)), "hawkes_mlp_set_data")
+
+    def train(self, steps, batch=512, lr=1e-3, seed=0):
+        loss = ctypes.c_double()
+        _check(lib().hawkes_mlp_train(self.m, int(steps), int(batch), float(lr), int(seed), ctypes.byref(loss)),
+               "hawkes_mlp_train")
+        return loss.value
+
+    def loss_grad(self, Xs, Ts):
+        Xs, Ts = _f32(Xs).reshape(-1, 7), _f32(Ts).reshape(-1, 7)
+        B = Xs.shape[0]
+        g = np.zeros(HAWKES_MLP_NPARAMS, dtype=np.float32)
+        Y = np.zeros((B, 7), dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().hawkes_mlp_loss_grad(self.m, B, Xs.ctypes.data_as(_F), Ts.ctypes.data_as(_F),
+                                          ctypes.byref(loss), g.ctypes.data_as(_F), Y.ctypes.data_as(_F)),
+               "hawkes_mlp_loss_grad")
+        return loss.value, g, Y
+
+    def predict(self, d_logp, count, d_out):
+        """Device pointers: d_logp[count x 6] -> d_out[count x 7] (queued)."""
+        _check(lib().hawkes_mlp_predict(self.m, int(count), _VP(int(d_logp)), _VP(int(d_out))),
+               "hawkes_mlp_predict")
+
+    def stats(self):
+        s = np.zeros(26)
+        _check(lib().hawkes_mlp_stats(self.m, _dp(s)), "hawkes_mlp_stats")
+        return s
+
+    def wait(self):
+        _check(lib().hawkes_mlp_wait(self.m), "hawkes_mlp_wait")
 
 
 # --- convenience wrapper ---------------------------------------------------

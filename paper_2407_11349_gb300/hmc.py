@@ -1,0 +1,362 @@
+"""Hamiltonian Monte Carlo on the cut posterior (Sec. 2.2), exact and
+surrogate-driven.
+
+The cut posterior is sampled by alternating (i) a fresh draw of every event
+location uniformly in its county, and (ii) a transition that leaves
+p(Theta | X, t) invariant.  The paper uses univariate Metropolis-Hastings for
+(ii); here it is HMC on eta = log(mu, tau_x, tau_t, theta, omega, h) with
+independent Normal(eta0, 2^2) priors (our choice; the paper does not state
+its priors) plus the log-transform Jacobian.
+
+Exact HMC evaluates the exact gradient at every leapfrog step.  Surrogate HMC
+runs the whole leapfrog trajectory on a neural-network approximation of the
+gradient (any fixed vector field gives a reversible, volume-preserving map)
+and accepts with the EXACT Hamiltonian at both ends under the current X, so
+the chain still targets p(Theta | X, t); a poor surrogate costs acceptance,
+not correctness.
+
+Chains advance in lockstep: the exact evaluations of all chains are one
+batched launch (``Batch``), the surrogate's predictions one network call.
+Step size: dual averaging (Hoffman and Gelman 2014); metric: a dense
+covariance estimate from windows of warmup draws.  Checkpoints (``save``/``load``) hold every piece of
+state, so a resumed run continues bit for bit.
+"""
+import time
+
+import numpy as np
+
+NAMES = ("mu", "tau_x", "tau_t", "theta", "omega", "h")
+PRIOR_SD = 2.0
+ETA_MAX = 30.0  # |log p| beyond this is treated as a divergent trajectory
+
+
+class Prior:
+    """Independent Normal(eta0, sd^2) on eta = log p, plus the Jacobian sum(eta)."""
+
+    def __init__(self, eta0, sd=PRIOR_SD):
+        self.eta0 = np.asarray(eta0, dtype=np.float64)
+        self.sd = float(sd)
+
+    def __call__(self, eta):
+        d = (eta - self.eta0) / self.sd
+        lp = -0.5 * np.sum(d * d, axis=-1) + np.sum(eta, axis=-1)
+        g = -d / self.sd + 1.0
+        return lp, g
+
+
+class HawkesTarget:
+    """Exact log-likelihood and gradient for C chains on one GPU.
+
+    Each chain owns a context with the same events and its own resample
+    stream; ``resample_eval`` draws new locations for every chain and then
+    evaluates (one captured graph), ``eval`` evaluates at fixed locations.
+    Returns the log-likelihood and its gradient in eta = log p.
+    """
+
+    def __init__(self, ds, n_chains, seed=0, device=0):
+        import torch
+
+        from .hawkes import HAWKES_F32, Batch, Hawkes, HawkesError
+
+        self.torch = torch
+        self.HawkesError = HawkesError
+        self.n_failed = 0
+        self.C = n_chains
+        self.stream = torch.cuda.Stream(device=device)
+        s = self.stream.cuda_stream
+        self.hks = [Hawkes(device, s).load(ds) for _ in range(n_chains)]
+        self.dp = torch.zeros((n_chains, 6), dtype=torch.float64, device=f"cuda:{device}")
+        self.dout = torch.zeros((n_chains, 7), dtype=torch.float64, device=f"cuda:{device}")
+        self.host = torch.zeros((n_chains, 7), dtype=torch.float64).pin_memory()
+        self.b_rs = Batch(self.hks, [seed] * n_chains, list(range(n_chains)), HAWKES_F32, s)
+        self.b_ev = Batch(self.hks, None, None, HAWKES_F32, s)
+        self.b_rs.capture(self.dp.data_ptr(), self.dout.data_ptr())
+        self.b_ev.capture(self.dp.data_ptr(), self.dout.data_ptr())
+        self.n_exact = 0
+        self.n_events = ds.n
+
+    def _run(self, batch, eta, iteration):
+        torch = self.torch
+        p = np.exp(np.asarray(eta, dtype=np.float64))
+        with torch.cuda.stream(self.stream):
+            self.dp.copy_(torch.from_numpy(p), non_blocking=False)
+        self.stream.synchronize()
+        batch.run(self.dp.data_ptr(), iteration, self.dout.data_ptr())
+        try:
+            batch.wait()
+        except self.HawkesError:
+            # a problem with unusable parameters or a non-finite result: its
+            # outputs are NaN and the sampler rejects that chain's move
+            self.n_failed += 1
+        with torch.cuda.stream(self.stream):
+            self.host.copy_(self.dout)
+        self.stream.synchronize()
+        out = self.host.numpy().copy()
+        self.n_exact += self.C
+        return out[:, 0], out[:, 1:] * p
+
+    def resample_eval(self, iteration, eta):
+        return self._run(self.b_rs, eta, iteration)
+
+    def eval(self, eta):
+        return self._run(self.b_ev, eta, 0)
+
+    def close(self):
+        self.b_rs.close()
+        self.b_ev.close()
+        for h in self.hks:
+            h.close()
+
+
+class SurrogateField:
+    """The network's (log-likelihood, eta-gradient) prediction for C chains."""
+
+    def __init__(self, mlp, n_chains, device=0):
+        import torch
+
+        self.torch = torch
+        self.mlp = mlp
+        self.C = n_chains
+        self.dq = torch.zeros((n_chains, 6), dtype=torch.float64, device=f"cuda:{device}")
+        self.dout = torch.zeros((n_chains, 7), dtype=torch.float64, device=f"cuda:{device}")
+        self.n_calls = 0
+
+    def __call__(self, eta):
+        torch = self.torch
+        self.dq.copy_(torch.from_numpy(np.asarray(eta, dtype=np.float64)))
+        torch.cuda.synchronize()
+        self.mlp.predict(self.dq.data_ptr(), self.C, self.dout.data_ptr())
+        self.mlp.wait()
+        out = self.dout.cpu().numpy()
+        self.n_calls += 1
+        return out[:, 0], out[:, 1:]
+
+
+class DualAveraging:
+    """Step-size adaptation of Hoffman and Gelman (2014), per chain."""
+
+    def __init__(self, eps0, delta=0.8, gamma=0.05, t0=10.0, kappa=0.75):
+        self.mu = np.log(10.0 * eps0)
+        self.delta, self.gamma, self.t0, self.kappa = delta, gamma, t0, kappa
+        self.hbar = np.zeros_like(eps0)
+        self.logeps_bar = np.zeros_like(eps0)
+        self.t = 0
+        self.logeps = np.log(eps0)
+
+    def update(self, accept_stat):
+        self.t += 1
+        w = 1.0 / (self.t + self.t0)
+        self.hbar = (1 - w) * self.hbar + w * (self.delta - accept_stat)
+        self.logeps = self.mu - np.sqrt(self.t) / self.gamma * self.hbar
+        eta = self.t ** (-self.kappa)
+        self.logeps_bar = eta * self.logeps + (1 - eta) * self.logeps_bar
+        return np.exp(self.logeps)
+
+    def final(self):
+        return np.exp(self.logeps_bar)
+
+
+class Sampler:
+    """Lockstep HMC for C chains on the cut posterior.
+
+    target:  object with resample_eval(iteration, eta) and eval(eta), each
+             returning (loglik[C], grad_eta[C, 6])
+    prior:   Prior
+    """
+
+    def __init__(self, target, prior, eta_init, n_leapfrog=10, seed=0, jitter=0.2, cut=True):
+        self.target = target
+        self.cut = bool(cut)  # False: keep the locations fixed (samples p(Theta | X, t) for one X)
+        self.prior = prior
+        self.q = np.array(eta_init, dtype=np.float64, copy=True)
+        self.C = self.q.shape[0]
+        self.L = int(n_leapfrog)
+        self.eps = np.full(self.C, 0.05)
+        self.cov = np.tile(np.eye(6), (self.C, 1, 1))  # metric: inverse mass (posterior covariance estimate)
+        self.chol = np.linalg.cholesky(self.cov)
+        self.rng = np.random.default_rng(seed)
+        self.jitter = float(jitter)  # step size drawn from eps * U(1 - jitter, 1 + jitter)
+        self.iteration = 0
+        self.divergent = 0
+        self.record = None  # list of (eta, loglik, grad) exact evaluations, when collecting
+
+    def _exact(self, eta, resample=False):
+        if resample:
+            ll, g = self.target.resample_eval(self.iteration, eta)
+        else:
+            ll, g = self.target.eval(eta)
+        if self.record is not None:
+            self.record.append((eta.copy(), ll.copy(), g.copy()))
+        lp, gp = self.prior(eta)
+        return ll + lp, g + gp
+
+    def _init_scale(self):
+        """Initial inverse mass from the gradient at the starting point: a
+        component whose log-density changes by g per unit starts with a
+        scale ~ 1/|g| (the posterior in eta is very narrow at large N)."""
+        _, g = self._exact(self.q, resample=self.cut)
+        self.set_cov(np.stack([np.diag(np.clip(1.0 / (gc * gc + 1e-12), 1e-12, 1.0)) for gc in g]))
+        self.eps = np.full(self.C, 0.1)
+
+    def set_cov(self, cov):
+        self.cov = np.array(cov, dtype=np.float64)
+        self.chol = np.linalg.cholesky(self.cov)
+
+    def _momentum(self):
+        # p ~ N(0, cov^-1): p = L^-T z with cov = L L^T
+        z = self.rng.standard_normal((self.C, 6))
+        return np.stack([np.linalg.solve(self.chol[c].T, z[c]) for c in range(self.C)])
+
+    def _kinetic(self, p):
+        return 0.5 * np.einsum("ci,cij,cj->c", p, self.cov, p)
+
+    def _velocity(self, p):
+        return np.einsum("cij,cj->ci", self.cov, p)
+
+    def transition(self, field=None):
+        """One cut-posterior iteration: new locations, then one HMC move.
+        field(eta) -> (loglik, grad) drives the trajectory (None: exact).
+        A trajectory that leaves |eta| <= ETA_MAX or turns non-finite is
+        divergent: it is rejected (its exact evaluations use the current
+        state instead).  Returns the acceptance probability of each chain."""
+        self.iteration += 1
+        lp0, g0 = self._exact(self.q, resample=self.cut)
+        p0 = self._momentum()
+        # a random step size per iteration (independent of the state) avoids
+        # trajectories that return to their start on near-Gaussian targets
+        eps = (self.eps * (1.0 + self.jitter * (2.0 * self.rng.random(self.C) - 1.0)))[:, None]
+        bad = np.zeros(self.C, dtype=bool)
+
+        def safe(q):
+            nonlocal bad
+            bad |= ~np.all(np.isfinite(q) & (np.abs(q) <= ETA_MAX), axis=1)
+            return np.where(bad[:, None], self.q, q)
+
+        def grad(q):
+            if field is None:
+                lp, g = self._exact(safe(q))
+            else:
+                lp, g = None, field(safe(q))[1] + self.prior(safe(q))[1]
+            bad[:] |= ~np.all(np.isfinite(g), axis=1)
+            return lp, np.where(bad[:, None], 0.0, g)
+
+        q = self.q.copy()
+        p = p0 + 0.5 * eps * (g0 if field is None else grad(q)[1])
+        lp1 = None
+        for step in range(self.L):
+            q = q + eps * self._velocity(p)
+            lpq, gq = grad(q)
+            p = p + (eps if step < self.L - 1 else 0.5 * eps) * gq
+            lp1 = lpq
+        if field is not None:
+            lp1, _ = self._exact(safe(q))
+        H0 = -lp0 + self._kinetic(p0)
+        H1 = -lp1 + self._kinetic(p)
+        log_a = np.where(np.isfinite(H1) & ~bad, H0 - H1, -np.inf)
+        a = np.exp(np.minimum(0.0, log_a))
+        u = self.rng.random(self.C)
+        take = (u < a) & ~bad
+        self.q[take] = q[take]
+        self.divergent = int(bad.sum())
+        return a
+
+    def warmup(self, n, field=None):
+        """Adapt the step size (dual averaging, every iteration) and the dense
+        metric: a fast window (first 15%), slow windows of doubling length
+        whose draws give a covariance estimate (shrunk towards its diagonal),
+        and a final fast window (last 10%).  Returns the iteration at which
+        the last slow window began (its draws are in the posterior's bulk)."""
+        self._init_scale()
+        da = DualAveraging(self.eps.copy())
+        start, end = int(0.15 * n), int(0.90 * n)
+        bounds, w, b = [], 25, start
+        while b < end:
+            e = end if end - (b + w) < 2 * w else b + w
+            bounds.append((b, e))
+            b, w = e, 2 * w
+        draws, last_start = [], start
+        for k in range(n):
+            a = self.transition(field)
+            self.eps = da.update(a)
+            for (w0, w1) in bounds:
+                if w0 <= k < w1:
+                    draws.append(self.q.copy())
+                if k == w1 - 1 and len(draws) > 10:
+                    D = np.stack(draws)  # (draws, C, 6)
+                    m = D.shape[0]
+                    cov = np.stack([np.cov(D[:, c].T) for c in range(self.C)])
+                    diag = np.stack([np.diag(np.diag(cv)) for cv in cov])
+                    cov = (m / (m + 5.0)) * cov + (5.0 / (m + 5.0)) * diag
+                    cov += np.stack([1e-10 * np.trace(cv) / 6 * np.eye(6) for cv in cov])
+                    self.set_cov(cov)
+                    draws = []
+                    da = DualAveraging(self.eps.copy())
+                    last_start = w0
+        self.eps = da.final()
+        return last_start
+
+    def sample(self, n, field=None):
+        out = np.zeros((self.C, n, 6))
+        acc = np.zeros(n)
+        t0 = time.perf_counter()
+        for k in range(n):
+            acc[k] = self.transition(field).mean()
+            out[:, k] = self.q
+        return out, acc, time.perf_counter() - t0
+
+    # ---- checkpoint -----------------------------------------------------
+    def state(self):
+        return {"q": self.q.copy(), "eps": self.eps.copy(), "cov": self.cov.copy(),
+                "iteration": self.iteration, "L": self.L, "jitter": self.jitter,
+                "rng": self.rng.bit_generator.state}
+
+    def set_state(self, st):
+        self.q = np.array(st["q"], dtype=np.float64)
+        self.eps = np.array(st["eps"], dtype=np.float64)
+        self.set_cov(st["cov"])
+        self.iteration = int(st["iteration"])
+        self.L = int(st["L"])
+        self.jitter = float(st.get("jitter", self.jitter))
+        self.rng.bit_generator.state = st["rng"]
+
+
+def save(path, sampler, mlp=None, train_X=None, train_Y=None):
+    """Checkpoint the sampler (and the surrogate: weights + its training set,
+    from which its standardisation is recomputed) to an .npz file."""
+    import json
+    st = sampler.state()
+    extra = {}
+    if mlp is not None:
+        extra["mlp_params"] = mlp.get_params()
+        extra["train_X"] = np.asarray(train_X)
+        extra["train_Y"] = np.asarray(train_Y)
+    np.savez(path, q=st["q"], eps=st["eps"], cov=st["cov"], iteration=st["iteration"], L=st["L"],
+             jitter=st["jitter"], rng=json.dumps(st["rng"]), **extra)
+
+
+def load(path, sampler, mlp=None):
+    import json
+    z = np.load(path, allow_pickle=False)
+    sampler.set_state({"q": z["q"], "eps": z["eps"], "cov": z["cov"], "iteration": int(z["iteration"]),
+                       "L": int(z["L"]), "jitter": float(z["jitter"]), "rng": json.loads(str(z["rng"]))})
+    if mlp is not None and "mlp_params" in z:
+        mlp.set_data(z["train_X"], z["train_Y"])
+        mlp.set_params(z["mlp_params"])
+
+
+def training_set(record, k_mad=25.0):
+    """Stack recorded exact evaluations into (X[n x 6], Y[n x 7]).  Rows with
+    a non-finite value, or with any column more than k_mad median absolute
+    deviations from that column's median, are dropped: leapfrog excursions
+    far outside the posterior (log-likelihoods many orders of magnitude
+    below the bulk) would otherwise set the network's standardisation."""
+    X = np.concatenate([r[0] for r in record])
+    Y = np.concatenate([np.column_stack([r[1], r[2]]) for r in record])
+    ok = np.all(np.isfinite(X), axis=1) & np.all(np.isfinite(Y), axis=1)
+    X, Y = X[ok], Y[ok]
+    Z = np.column_stack([X, Y])
+    med = np.median(Z, axis=0)
+    mad = np.median(np.abs(Z - med), axis=0)
+    mad = np.where(mad > 0, mad, np.maximum(np.abs(med), 1.0) * 1e-12)
+    keep = np.all(np.abs(Z - med) <= k_mad * mad, axis=1)
+    return X[keep], Y[keep]

@@ -242,6 +242,58 @@ def voronoi_dataset(n, T=1200.0, n_cells=3143, width=4500.0, height=2800.0, seed
     return Dataset(t, x, y, county, counties, DEFAULT_PARAMS, name)
 
 
+def clustered_dataset(n, T=100.0, nx=20, ny=20, cell=50.0, seed=0, params=DEFAULT_PARAMS,
+                      events_per_centre=40, name=""):
+    """Events whose structure matches the model's parameters (for samplers):
+    background events scattered around uniform space-time centres with
+    Gaussian offsets (sd tau_x in space, tau_t in time), plus branching
+    offspring (Poisson(theta) children per event, Exp(omega) delays, Gaussian
+    spatial offsets of sd h s_c of the parent's county), kept inside the
+    box and (0, T], subsampled to exactly n events.  Counties: an nx x ny
+    grid of squares with LogNormal(0, 1) densities."""
+    rng = np.random.default_rng(seed)
+    mu, tx, tt, th, om, h = params
+    counties = grid_counties(nx, ny, cell, rng)
+    sc = counties.scale()
+    W, H = nx * cell, ny * cell
+
+    def county_of(x, y):
+        i = np.clip((x // cell).astype(int), 0, nx - 1)
+        j = np.clip((y // cell).astype(int), 0, ny - 1)
+        return (j * nx + i).astype(np.int32)
+
+    m_imm = int(1.3 * n * (1.0 - th)) + 10
+    while True:
+        K = max(1, m_imm // events_per_centre)
+        cx, cy, ct = rng.uniform(0, W, K), rng.uniform(0, H, K), rng.uniform(0, T, K)
+        k = rng.integers(0, K, m_imm)
+        x = cx[k] + rng.normal(0, tx, m_imm)
+        y = cy[k] + rng.normal(0, tx, m_imm)
+        t = ct[k] + rng.normal(0, tt, m_imm)
+        ok = (x >= 0) & (x < W) & (y >= 0) & (y < H) & (t > 0) & (t <= T)
+        X, Y, Tt = [x[ok]], [y[ok]], [t[ok]]
+        gx, gy, gt = x[ok], y[ok], t[ok]
+        while gt.size:
+            kids = rng.poisson(th, gt.size)
+            px, py, pt = np.repeat(gx, kids), np.repeat(gy, kids), np.repeat(gt, kids)
+            sd = h * sc[county_of(px, py)]
+            cxk = px + rng.normal(0, 1, px.size) * sd
+            cyk = py + rng.normal(0, 1, py.size) * sd
+            ctk = pt + rng.exponential(1.0 / om, pt.size)
+            ok = (cxk >= 0) & (cxk < W) & (cyk >= 0) & (cyk < H) & (ctk <= T)
+            gx, gy, gt = cxk[ok], cyk[ok], ctk[ok]
+            X.append(gx), Y.append(gy), Tt.append(gt)
+        x, y, t = np.concatenate(X), np.concatenate(Y), np.concatenate(Tt)
+        if t.size >= n:
+            break
+        m_imm = int(m_imm * 1.5)
+    keep = np.sort(rng.choice(t.size, n, replace=False))
+    x, y, t = x[keep], y[keep], t[keep]
+    order = np.argsort(t, kind="stable")
+    x, y, t = x[order], y[order], t[order]
+    return Dataset(t, x, y, county_of(x, y), counties, params, name or f"clustered{n}")
+
+
 def integer_day_times(ds, seed=0):
     """Copy of ``ds`` with times rounded up to whole days (many exact ties)."""
     t = np.maximum(np.ceil(ds.t), 1.0)

@@ -1,0 +1,125 @@
+"""HMC drivers and diagnostics on the host, against closed forms (no GPU).
+
+Targets here are Gaussians whose posterior (likelihood x Normal(eta0, 2^2)
+prior x Jacobian e^{sum eta}) is Gaussian in closed form, so the samplers'
+means and variances can be judged within Monte Carlo error; the surrogate is
+deliberately biased, and the exact accept step must still remove the bias.
+"""
+import numpy as np
+import pytest
+
+from paper_2407_11349_gb300 import diagnostics as dg
+from paper_2407_11349_gb300 import hmc
+
+
+def ar1(rho, chains, n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.zeros((chains, n))
+    e = rng.standard_normal((chains, n)) * np.sqrt(1 - rho ** 2)
+    x[:, 0] = rng.standard_normal(chains)
+    for t in range(1, n):
+        x[:, t] = rho * x[:, t - 1] + e[:, t]
+    return x
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5, 0.9])
+def test_ess_matches_ar1_closed_form(rho):
+    x = ar1(rho, 4, 20000, seed=int(10 * rho))
+    expect = x.size * (1 - rho) / (1 + rho)
+    got = dg.ess(x)
+    assert abs(got / expect - 1) < 0.1, (got, expect)
+    assert abs(dg.bulk_ess(x) / expect - 1) < 0.12
+
+
+def test_rhat_detects_shifted_chains():
+    x = ar1(0.3, 4, 4000, seed=3)
+    assert dg.rhat(x) < 1.01
+    y = x.copy()
+    y[0] += 1.0
+    assert dg.rhat(y) > 1.05
+    assert dg.tail_ess(x) > 1000
+
+
+class GaussTarget:
+    """log-likelihood -1/2 sum ((eta - m)/s)^2, no dependence on locations."""
+
+    def __init__(self, m, s, C):
+        self.m, self.s, self.C = np.asarray(m), np.asarray(s), C
+        self.n_exact = 0
+
+    def eval(self, eta):
+        self.n_exact += eta.shape[0]
+        d = (eta - self.m) / self.s
+        return -0.5 * np.sum(d * d, axis=1), -d / self.s
+
+    def resample_eval(self, iteration, eta):
+        return self.eval(eta)
+
+
+def posterior(m, s, eta0, sd=hmc.PRIOR_SD):
+    prec = 1 / s ** 2 + 1 / sd ** 2
+    return (m / s ** 2 + eta0 / sd ** 2 + 1.0) / prec, 1 / prec
+
+
+M = np.array([0.3, -1.0, 2.0, 0.0, 1.5, -0.5])
+S = np.array([0.1, 0.3, 0.05, 0.2, 0.5, 0.15])
+ETA0 = np.zeros(6)
+
+
+def _run(field, seed, n=1500):
+    """Warmup with exact gradients (as the pipeline does), then sample with
+    ``field`` driving the trajectories."""
+    C = 4
+    tgt = GaussTarget(M, S, C)
+    smp = hmc.Sampler(tgt, hmc.Prior(ETA0), np.tile(M, (C, 1)) + 0.01, n_leapfrog=8, seed=seed)
+    smp.warmup(300)
+    draws, acc, _ = smp.sample(n, field)
+    return draws, acc, tgt
+
+
+def _check_posterior(draws, rhat_max=1.05):
+    mean, var = posterior(M, S, ETA0)
+    summ = dg.summary(draws, hmc.NAMES)
+    for k, nm in enumerate(hmc.NAMES):
+        x = draws[:, :, k]
+        assert abs(x.mean() - mean[k]) < 4.5 * summ[nm]["mcse"], (nm, x.mean(), mean[k])
+        assert abs(x.var() / var[k] - 1) < 0.25, (nm, x.var(), var[k])
+        assert summ[nm]["rhat"] < rhat_max
+
+
+def test_exact_hmc_recovers_gaussian_posterior():
+    draws, acc, tgt = _run(None, seed=1)
+    assert acc.mean() > 0.6
+    _check_posterior(draws)
+
+
+def test_surrogate_hmc_with_biased_field_is_still_exact():
+    # the surrogate's gradient points at the wrong mean with the wrong scale
+    def field(eta):
+        d = (eta - (M + 0.3 * S)) / (1.3 * S)
+        return None, -d / (1.3 * S)
+
+    draws, acc, tgt = _run(field, seed=2, n=3000)
+    assert 0.05 < acc.mean() < 0.99
+    # exactness: means within Monte Carlo error and variances right, although
+    # the trajectories follow the wrong field (mixing is slower: looser R-hat)
+    _check_posterior(draws, rhat_max=1.1)
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    C = 2
+    t1 = GaussTarget(M, S, C)
+    a = hmc.Sampler(t1, hmc.Prior(ETA0), np.tile(M, (C, 1)), n_leapfrog=5, seed=9)
+    a.warmup(40)
+    for _ in range(10):
+        a.transition()
+    path = tmp_path / "ck.npz"
+    hmc.save(path, a)
+    ref = [a.transition().copy() for _ in range(15)]
+    ref_q = a.q.copy()
+    t2 = GaussTarget(M, S, C)
+    b = hmc.Sampler(t2, hmc.Prior(ETA0), np.zeros((C, 6)), n_leapfrog=1, seed=0)
+    hmc.load(path, b)
+    got = [b.transition().copy() for _ in range(15)]
+    assert np.array_equal(np.stack(ref), np.stack(got))
+    assert np.array_equal(ref_q, b.q)
