@@ -329,6 +329,16 @@ int hawkes_mlp_wait(hawkes_mlp* mlp);
 int64_t hawkes_num_events(const hawkes_ctx* ctx);
 
 /*
+ * Failure-detection self-check (synchronous).  Device-side waits (on the
+ * sweep's TMA barriers) are bounded: after about 2 s a wait gives up, latches
+ * HAWKES_ERR_TIMEOUT and the kernel returns, leaving the context usable.
+ * This launches one thread that waits on a barrier nothing completes and
+ * returns HAWKES_OK if that wait gave up and reported HAWKES_ERR_TIMEOUT as
+ * designed (*seconds, optional: how long it took), an error otherwise.
+ */
+int hawkes_check_bounded_wait(hawkes_ctx* ctx, double* seconds);
+
+/*
  * Allocation-free log-likelihood and gradient (no counterpart in the paper;
  * a deployment convenience of this library).
  *

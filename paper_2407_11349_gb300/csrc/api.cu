@@ -26,6 +26,7 @@ __global__ void k_tri_check(const int32_t*, int32_t, int32_t, int*);
 __global__ void k_resample(const int32_t*, int64_t, const double*, const double*, const int32_t*,
                            const int32_t*, uint64_t, uint64_t, uint64_t, const uint64_t*, double*,
                            double*);
+__global__ void k_wait_selftest(int*);
 // sweep.cu
 cudaError_t sweep_setup_attributes();
 int sweep_num_variants();
@@ -478,6 +479,24 @@ int hawkes_loglik_rows(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, do
     if (c->n == 0) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
     return sync_loglik(c, p, flags, 0, c->n, out7, rows);
+}
+
+int hawkes_check_bounded_wait(hawkes_ctx* c, double* seconds) {
+    if (!c) return HAWKES_ERR_ARG;
+    DeviceGuard g(c->device);
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    const int pending = take_device_error(c);  // do not mistake an earlier error for the test's
+    if (pending != HAWKES_OK) return pending;
+    HK_CUDA(cudaEventRecord(c->pev[0], c->stream));
+    k_wait_selftest<<<1, 32, 0, c->stream>>>(c->ctr);
+    HK_CUDA(cudaGetLastError());
+    HK_CUDA(cudaEventRecord(c->pev[1], c->stream));
+    HK_CUDA(cudaEventSynchronize(c->pev[1]));
+    float ms = 0.f;
+    HK_CUDA(cudaEventElapsedTime(&ms, c->pev[0], c->pev[1]));
+    if (seconds) *seconds = ms / 1000.0;
+    const int err = take_device_error(c);
+    return err == HAWKES_ERR_TIMEOUT ? HAWKES_OK : (err == HAWKES_OK ? HAWKES_ERR_STATE : err);
 }
 
 int hawkes_sweep_variants(void) { return sweep_num_variants(); }

@@ -102,8 +102,10 @@ constexpr double LOG2E = 1.4426950408889634;
 constexpr double CLIP = 1e-40;
 constexpr double TWO_PI = 6.283185307179586;
 
-// Bounded spin: iterations of mbarrier.try_wait before a wait gives up.
-constexpr long long SPIN_LIMIT = 1ll << 22;
+// Bounded waits: a wait on an mbarrier gives up after WAIT_CYCLES SM clock
+// cycles (about 2 s at 2 GHz) or SPIN_LIMIT polls, whichever comes first.
+constexpr long long SPIN_LIMIT = 1ll << 30;
+constexpr long long WAIT_CYCLES = 4000000000ll;
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -152,10 +154,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for phase `parity` of `bar` to complete; false if the bounded spin gave up.
+// Wait for phase `parity` of `bar` to complete; false if the bounded wait gave up.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (long long k = 0; k < SPIN_LIMIT; ++k)
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (long long k = 0; k < SPIN_LIMIT; ++k) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((k & 63) == 63 && clock64() - t0 > WAIT_CYCLES) return false;
+    }
     return false;
 }
 

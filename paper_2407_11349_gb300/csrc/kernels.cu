@@ -428,4 +428,16 @@ __global__ void k_resample(const int32_t* __restrict__ county, int64_t n,
     }
 }
 
+// Self-check of the bounded wait: one thread waits on an mbarrier that nothing
+// ever completes; the wait must give up and latch HAWKES_ERR_TIMEOUT.
+__global__ void k_wait_selftest(int* ctr) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) set_error(ctr, HAWKES_ERR_TIMEOUT);
+}
+
 }  // namespace hk

@@ -61,6 +61,7 @@ _SIGS = {
     "hawkes_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_profile)]),
     "hawkes_num_events": (ctypes.c_int64, [_VP]),
     "hawkes_sweep_variants": (ctypes.c_int, []),
+    "hawkes_check_bounded_wait": (ctypes.c_int, [_VP, _D]),
     "hawkes_set_sweep_variant": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hawkes_get_sweep_variant": (ctypes.c_int, [_VP]),
     "hawkes_tune": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_params), ctypes.c_uint32, ctypes.c_int,
@@ -446,6 +447,12 @@ class Hawkes:
         if on is not None:
             hawkes_profile_enable(self.ctx, on)
         return hawkes_profile_read(self.ctx)
+
+    def check_bounded_wait(self):
+        """Seconds the device-side bounded wait took to give up (raises if it did not)."""
+        sec = ctypes.c_double()
+        _check(lib().hawkes_check_bounded_wait(self.ctx, ctypes.byref(sec)), "hawkes_check_bounded_wait")
+        return sec.value
 
     def tune(self, params, flags=HAWKES_F32, reps=2):
         return hawkes_tune(self.ctx, params, flags, reps)

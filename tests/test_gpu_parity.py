@@ -188,6 +188,19 @@ def test_invalid_input_is_reported(hk):
     assert np.isfinite(ll)
 
 
+def test_bounded_wait_gives_up_and_context_survives(hk):
+    """A device-side wait on a barrier that nothing completes must give up
+    within its bound (about 2 s), report HAWKES_ERR_TIMEOUT, and leave the
+    context usable."""
+    sec = hk.check_bounded_wait()
+    assert 0.2 < sec < 20.0
+    ds = small_grid(500, seed=14)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref = oracle.loglik_grad(ds.t, ds.x, ds.y, P0, s=ds.s)
+    ll, g = hk.loglik_grad(P0)
+    assert abs(ll - ref[0]) <= TOL_LL32 * abs(ref[0])
+
+
 def test_c2_sampled_rows_and_paths(hk):
     """N=100,000 (60x60 grid, 1,200 d) after one resample: FP32 rows against the
     oracle one by one on sampled rows; FP32 totals against the FP64 GPU path."""
