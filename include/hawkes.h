@@ -66,7 +66,16 @@ enum {
     HAWKES_F32 = 0,      /* pair terms in FP32 (SFU exp2), per-row and global sums in FP64 */
     HAWKES_F64 = 1,      /* every pair term in FP64 (slow on GB300: reference path) */
     HAWKES_MODEL2 = 0,   /* source bandwidth h * s_j from the county scale (eq. 3) */
-    HAWKES_MODEL1 = 2    /* s_j = 1 for every event (eq. 2) */
+    HAWKES_MODEL1 = 2,   /* s_j = 1 for every event (eq. 2) */
+    /*
+     * FP32 path only: skip tiles of the pair sweep whose every term is
+     * exactly 0 in FP32 (flushed to zero): pairs farther apart in time than
+     * sqrt(128) tau_t sqrt(2 / log2 e) contribute no background, and sources
+     * earlier by more than (128 + max_j(-2 log2 s_j)) / (omega log2 e)
+     * contribute no excitation.  The result is the same as without the flag
+     * (the skipped terms are exact zeros); only the work shrinks.
+     */
+    HAWKES_SKIP_UNDERFLOW = 4
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -217,7 +226,7 @@ int hawkes_tune(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags, in
  *                      do not change their events while the batch exists
  *   seeds[P], streams[P]  resample keys of each problem (Philox key as in
  *                      hawkes_resample_locations), or both NULL for no resample
- *   flags              HAWKES_F32, optionally | HAWKES_MODEL1
+ *   flags              HAWKES_F32, optionally | HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW
  *   cuda_stream        stream for the batch's work, or NULL for its own
  */
 typedef struct hawkes_batch hawkes_batch;

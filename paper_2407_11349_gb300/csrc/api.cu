@@ -12,7 +12,7 @@ namespace hk {
 __global__ void k_setup(double*, double*, double*, const int32_t*, int32_t, const double*, int64_t,
                         int64_t, int, double*, int32_t*, int32_t*, double*, int*);
 __global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
-                       const hawkes_params*, int, int, int64_t, int64_t, Rec*, double*, double*,
+                       const hawkes_params*, int, int, int, int64_t, int64_t, Rec*, double*, double*,
                        int*, double*);
 __global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
                            int, int*, int*, double*, double*);
@@ -166,11 +166,12 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
                    int64_t re, double* d_out, double* d_rows9) {
     const bool f64 = (flags & HAWKES_F64) != 0;
     const int model1 = (flags & HAWKES_MODEL1) ? 1 : 0;
+    const int skip = (!f64 && (flags & HAWKES_SKIP_UNDERFLOW)) ? 1 : 0;
     const int prep_grid = grid_for(c, c->npad);
     HK_TRY(timed(c, HAWKES_K_PREP, [&] {
         k_prep<<<prep_grid, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->tb, d_params, model1,
-                                                  f64 ? 0 : 1, c->n, c->npad, c->rec, c->acc, c->cc,
-                                                  c->ctr, c->fix7);
+                                                  f64 ? 0 : 1, skip, c->n, c->npad, c->rec, c->acc,
+                                                  c->cc, c->ctr, c->fix7);
     }));
     if (!f64) {
         const bool sym = (rb == 0 && re == c->n);
@@ -210,7 +211,7 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
 int sync_loglik(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int64_t rb, int64_t re,
                 double* out7, double* rows_host) {
     if (!params_ok(p)) return HAWKES_ERR_ARG;
-    if ((flags & ~3u) != 0) return HAWKES_ERR_ARG;
+    if ((flags & ~7u) != 0) return HAWKES_ERR_ARG;
     HK_CUDA(cudaMemcpyAsync(c->params_dev, p, sizeof(hawkes_params), cudaMemcpyHostToDevice,
                             c->stream));
     double* d_rows9 = nullptr;
@@ -371,6 +372,8 @@ int hawkes_set_events(hawkes_ctx* c, int64_t n, const double* t, const double* x
         cudaMemcpyAsync(c->scale_c, county_scale, n_counties * sizeof(double), cudaMemcpyHostToDevice,
                         st) != cudaSuccess)
         return fail(HAWKES_ERR_CUDA);
+    if (cudaMemsetAsync(c->ctr + CT_CEMAX, 0, sizeof(int), st) != cudaSuccess)
+        return fail(HAWKES_ERR_CUDA);
     rc = timed(c, HAWKES_K_OTHER, [&] {
         k_setup<<<grid_for(c, npad), 256, 0, st>>>(c->t, c->x, c->y, c->county, n_counties,
                                                    c->scale_c, n, npad, x ? 1 : 0, c->s, c->lo,
@@ -467,7 +470,7 @@ int hawkes_loglik_grad(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, in
 int hawkes_loglik_grad_async(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
                              double* d_out) {
     if (!c || !d_params || !d_out) return HAWKES_ERR_ARG;
-    if ((flags & ~3u) != 0) return HAWKES_ERR_ARG;
+    if ((flags & ~7u) != 0) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
     return enqueue_loglik(c, d_params, flags, 0, c->n, d_out, nullptr);
@@ -514,7 +517,8 @@ int hawkes_tune(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int reps,
                 double* ms) {
     if (!c || !p || reps < 1) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
-    if (!params_ok(p) || (flags & ~(uint32_t)HAWKES_MODEL1) != 0) return HAWKES_ERR_ARG;
+    if (!params_ok(p) || (flags & ~(uint32_t)(HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW)) != 0)
+        return HAWKES_ERR_ARG;
     DeviceGuard g(c->device);
     const bool prof = c->prof;
     const hawkes_profile saved = c->pacc;

@@ -12,7 +12,7 @@
 
 namespace hk {
 __global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
-                       const hawkes_params*, int, int, int64_t, int64_t, Rec*, double*, double*,
+                       const hawkes_params*, int, int, int, int64_t, int64_t, Rec*, double*, double*,
                        int*, double*);
 __global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
                            int, int*, int*, double*, double*);
@@ -121,6 +121,7 @@ int build_items(hawkes_batch* b, int variant, int chunk, int order) {
 int enqueue(hawkes_batch* b, const hawkes_params* d_params, double* d_out, bool time_sweep) {
     cudaStream_t st = b->stream;
     const int model1 = (b->flags & HAWKES_MODEL1) ? 1 : 0;
+    const int skip = (b->flags & HAWKES_SKIP_UNDERFLOW) ? 1 : 0;
     const int P = static_cast<int>(b->probs.size());
     for (int p = 0; p < P; ++p) {
         hawkes_ctx* c = b->probs[p];
@@ -129,8 +130,8 @@ int enqueue(hawkes_batch* b, const hawkes_params* d_params, double* d_out, bool 
         if (b->resample)
             k_resample<<<g, 256, 0, st>>>(c->county, c->n, c->tri_xy, c->tri_cum, c->cfirst, c->clast,
                                           b->seeds[p], b->streams[p], 0, b->d_iter, c->x, c->y);
-        k_prep<<<g, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->tb, d_params + p, model1, 1, c->n,
-                                  c->npad, c->rec, c->acc, c->cc, c->ctr, c->fix7);
+        k_prep<<<g, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->tb, d_params + p, model1, 1, skip,
+                                  c->n, c->npad, c->rec, c->acc, c->cc, c->ctr, c->fix7);
     }
     HB_CUDA(cudaMemsetAsync(b->d_ctr + CT_WORK, 0, sizeof(int), st));
     if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[0], st));
@@ -176,7 +177,8 @@ int hawkes_batch_create(hawkes_batch** out, hawkes_ctx* const* problems, int32_t
                         void* cuda_stream) {
     if (!out) return HAWKES_ERR_ARG;
     *out = nullptr;
-    if (!problems || n_problems < 1 || (flags & ~static_cast<uint32_t>(HAWKES_MODEL1)) != 0 ||
+    if (!problems || n_problems < 1 ||
+        (flags & ~static_cast<uint32_t>(HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW)) != 0 ||
         (seeds == nullptr) != (streams == nullptr))
         return HAWKES_ERR_ARG;
     const int dev = problems[0] ? problems[0]->device : -1;
@@ -213,7 +215,8 @@ int hawkes_batch_create(hawkes_batch** out, hawkes_ctx* const* problems, int32_t
         if ((rc = st_of(cudaMemsetAsync(b->d_ctr, 0, CT_COUNT * sizeof(int), b->stream)))) break;
         if ((rc = st_of(cudaMemsetAsync(b->d_iter, 0, sizeof(uint64_t), b->stream)))) break;
         std::vector<ProbDesc> descs;
-        for (auto* c : b->probs) descs.push_back(ProbDesc{c->rec, c->lo, c->hi, c->tb, c->cc, c->acc, c->n, c->npad});
+        for (auto* c : b->probs)
+            descs.push_back(ProbDesc{c->t, c->rec, c->lo, c->hi, c->tb, c->cc, c->acc, c->n, c->npad});
         if ((rc = st_of(cudaMalloc(&b->d_probs, descs.size() * sizeof(ProbDesc))))) break;
         if ((rc = st_of(cudaMemcpyAsync(b->d_probs, descs.data(), descs.size() * sizeof(ProbDesc),
                                         cudaMemcpyHostToDevice, b->stream))))

@@ -62,6 +62,7 @@ constexpr float PAD_T = 1.0e15f;
 // One problem of the pair sweep: its staged records, tie ranges, time bases,
 // per-call constants and accumulators (all device pointers).
 struct ProbDesc {
+    const double* t;  // FP64 times (for the underflow-skip bounds)
     const Rec* rec;
     const int32_t* lo;
     const int32_t* hi;
@@ -85,6 +86,8 @@ enum {
     CC_MU, CC_TX, CC_TT, CC_TH, CC_OM, CC_H,
     CC_TN,          // t_N
     CC_FLAGTHR,     // rows with lambda below this are recomputed in FP64
+    CC_SKIPDT,      // > 0: skip tiles whose smallest time gap (scaled) exceeds this
+    CC_SKIPDTB,     // the background-only part of that bound (sqrt(128))
     CC_VALID,       // 1 if the parameters are valid
     CC_COUNT
 };
@@ -95,6 +98,7 @@ enum {
     CT_FIX,         // number of rows queued for FP64 recomputation
     CT_ERR,         // latched error status (0 or a HAWKES_ERR_* value)
     CT_DONE,        // finished-block counter
+    CT_CEMAX,       // bits of max(0, max_j -2 log2 s_j), set when the events are loaded
     CT_COUNT = 8
 };
 

@@ -44,6 +44,8 @@ __global__ void k_setup(double* t, double* x, double* y, const int32_t* county, 
             else se = scale_c[c];
             if (!(se > 0.0) || !isfinite(se)) set_error(ctr, HAWKES_ERR_ARG);
             s[e] = se;
+            const float ce = static_cast<float>(-2.0 * log2(se));
+            if (ce > 0.f) atomicMax(ctr + CT_CEMAX, __float_as_int(ce));
             if (xy_given) {
                 if (!isfinite(x[e]) || !isfinite(y[e])) set_error(ctr, HAWKES_ERR_ARG);
             } else {
@@ -93,10 +95,11 @@ __device__ __forceinline__ Consts make_consts(const hawkes_params* P) {
 }
 
 // Zero the accumulators, reset the counters and (FP32 path) stage the event table.
+// skip: evaluate only tiles whose terms can be nonzero in FP32 (see CC_SKIPDT).
 __global__ void k_prep(const double* __restrict__ t, const double* __restrict__ x,
                        const double* __restrict__ y, const double* __restrict__ s,
                        const double* __restrict__ tb, const hawkes_params* P, int model1,
-                       int stage, int64_t n, int64_t npad, Rec* __restrict__ rec,
+                       int stage, int skip, int64_t n, int64_t npad, Rec* __restrict__ rec,
                        double* __restrict__ acc, double* __restrict__ cc, int* ctr,
                        double* fix7) {
     const Consts k = make_consts(P);
@@ -110,6 +113,14 @@ __global__ void k_prep(const double* __restrict__ t, const double* __restrict__ 
         // Terms below 2^-126 flush to zero in the FP32 path; rows whose rate is
         // within 1e9 x (n such terms) of that are recomputed in FP64.
         cc[CC_FLAGTHR] = 1e9 * (double)n * 1.1754943508222875e-38 * (k.mu * k.cB + k.th * k.cE);
+        // A background term is exactly 0 in FP32 (flush to zero) when its
+        // base-2 exponent dt~^2 + r~^2 exceeds 126; an excitation term when
+        // omega~ dt~ + beta r~^2 - ce exceeds 126.  With 2 units of margin, a
+        // tile whose smallest scaled time gap exceeds both bounds contributes
+        // exactly nothing.
+        const double cemax = model1 ? 0.0 : static_cast<double>(__int_as_float(ctr[CT_CEMAX]));
+        cc[CC_SKIPDTB] = skip ? sqrt(128.0) : 0.0;
+        cc[CC_SKIPDT] = skip ? fmax(sqrt(128.0), (cemax + 128.0) / k.omt) : 0.0;
         cc[CC_VALID] = k.valid ? 1.0 : 0.0;
         ctr[CT_WORK] = 0;
         ctr[CT_FIX] = 0;

@@ -25,7 +25,7 @@
 
 namespace hk {
 __global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
-                       const hawkes_params*, int, int, int64_t, int64_t, Rec*, double*, double*,
+                       const hawkes_params*, int, int, int, int64_t, int64_t, Rec*, double*, double*,
                        int*, double*);
 __global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
                            int, int*, int*, double*, double*);
@@ -241,7 +241,7 @@ extern "C" int hawkes_loglik_grad_noalloc(const double* d_t, const double* d_x, 
     k_na_setup<<<grid, 256, 0, st>>>(d_t, d_x, d_y, d_s, n, npad, c.t, c.x, c.y, c.s, c.lo, c.hi,
                                      c.tb, c.ctr);
     k_na_items<<<1, 32, 0, st>>>(n, tr, c.items);
-    k_prep<<<grid, 256, 0, st>>>(c.t, c.x, c.y, c.s, c.tb, d_params, model1, 1, n, npad, c.rec,
+    k_prep<<<grid, 256, 0, st>>>(c.t, c.x, c.y, c.s, c.tb, d_params, model1, 1, 0, n, npad, c.rec,
                                  c.acc, c.cc, c.ctr, c.fix7);
     if (launch_sweep(&c, true, 0, n) != cudaSuccess) return HAWKES_ERR_CUDA;
     k_finalize<<<c.final_blocks, 256, 0, st>>>(c.acc, c.t, c.cc, npad, 0, n, 1, c.fixlist, c.ctr,

@@ -229,6 +229,16 @@ __global__ void __launch_bounds__(THREADS, MINB)
         const float2 nomt = f2(-omt, -omt);
         const double kt = cc[CC_KT];
         const int64_t n = HK_PD(n);
+        const double skipdt = cc[CC_SKIPDT], skipdtb = cc[CC_SKIPDTB];
+        if (SYM && skipdt > 0.0) {  // whole item below the FP32 underflow bound
+            const double* tt = HK_PD(t);
+            const int64_t lastc = min(static_cast<int64_t>(je) * TC, n) - 1;
+            const double gap = (tt[min(I * G::TR, n - 1)] - tt[lastc]) * kt;
+            if (gap > skipdt) {
+                __syncthreads();
+                continue;
+            }
+        }
 
         const int64_t r0 = I * G::TR + warp * G::WROWS;  // warp's first row
         bool live = r0 < n;
@@ -280,7 +290,16 @@ __global__ void __launch_bounds__(THREADS, MINB)
             pendbits &= ~(1u << buf);
             const int jt = jb + J;
             const int j0 = jt * TC;
-            if (live) {
+            bool run = live;
+            if (live && skipdt > 0.0) {  // this warp's rows against this tile
+                const double* tt = HK_PD(t);
+                const int64_t rl = min(r0 + G::WROWS, n) - 1;
+                const int64_t cf = j0, cl = min(static_cast<int64_t>(j0) + TC, n) - 1;
+                const double before = (tt[r0] - tt[cl]) * kt;   // columns entirely earlier
+                const double after = (tt[cf] - tt[rl]) * kt;    // columns entirely later
+                if (before > skipdt || (after > skipdtb)) run = false;
+            }
+            if (run) {
                 const float dT = static_cast<float>((trow - HK_PD(tb)[jt]) * kt);
 #pragma unroll
                 for (int p = 0; p < RP; ++p) rr.tp[p] = f2(t0[2 * p] + dT, t0[2 * p + 1] + dT);
@@ -445,7 +464,7 @@ std::vector<int4> sweep_items_batch(const std::vector<int64_t>& ns, int v, int c
 std::vector<int4> sweep_items(int64_t n, int v) { return sweep_items_batch({n}, v, CHUNK, 0); }
 
 static ProbDesc desc_of(const hawkes_ctx* c) {
-    return ProbDesc{c->rec, c->lo, c->hi, c->tb, c->cc, c->acc, c->n, c->npad};
+    return ProbDesc{c->t, c->rec, c->lo, c->hi, c->tb, c->cc, c->acc, c->n, c->npad};
 }
 
 cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end) {

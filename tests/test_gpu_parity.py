@@ -16,8 +16,8 @@ import pytest
 
 import oracle
 from paper_2407_11349_gb300 import synth
-from paper_2407_11349_gb300.hawkes import (HAWKES_F32, HAWKES_F64, HAWKES_MODEL1, Hawkes,
-                                           HawkesError)
+from paper_2407_11349_gb300.hawkes import (HAWKES_F32, HAWKES_F64, HAWKES_MODEL1,
+                                           HAWKES_SKIP_UNDERFLOW, Hawkes, HawkesError)
 
 pytestmark = pytest.mark.gpu
 
@@ -186,6 +186,32 @@ def test_invalid_input_is_reported(hk):
         hk.loglik_grad(P0, HAWKES_F32, 50, 10)
     ll, g = hk.loglik_grad(P0)  # the context stays usable
     assert np.isfinite(ll)
+
+
+@pytest.mark.parametrize("ties", [False, True])
+def test_underflow_skip_matches_oracle(hk, ties):
+    """Skipping tiles whose terms are exact FP32 zeros changes nothing: a
+    6,000-event workload over 1,200 days (most pairs far apart in time)."""
+    ds = synth.grid_dataset(6000, 1200.0, 20, 20, seed=15)
+    if ties:
+        ds = synth.integer_day_times(ds)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle_rows(ds)
+    for p in (P0, (0.5, 20.0, 7.0, 0.3, 2.0, 2.0)):
+        ref, rows = oracle_rows(ds, p)
+        ll, g = hk.loglik_grad(p, HAWKES_F32 | HAWKES_SKIP_UNDERFLOW)
+        assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, "skip")
+        ll2, g2 = hk.loglik_grad(p, HAWKES_F32 | HAWKES_SKIP_UNDERFLOW, 1000, 5000)
+        w = oracle.loglik_grad(ds.t, ds.x, ds.y, p, s=ds.s, row_begin=1000, row_end=5000)
+        assert_close(ll2, g2, w, rows[1000:5000], TOL_LL32, TOL_G32, "skip window")
+
+
+def test_underflow_skip_c2_matches_full(hk):
+    ds = synth.config_dataset("c2")
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    full, rows = hk.loglik_rows(P0, HAWKES_F32)
+    ll, g = hk.loglik_grad(P0, HAWKES_F32 | HAWKES_SKIP_UNDERFLOW)
+    assert_close(ll, g, full, rows, 1e-9, 1e-8, "skip vs full")
 
 
 def test_bounded_wait_gives_up_and_context_survives(hk):
