@@ -226,6 +226,16 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
     n0 = tgt.n_exact
     d_su, acc_su, t_su = su.sample(draws, field)
     ev_su = tgt.n_exact - n0
+    # the paper's sampler: univariate Metropolis-Hastings, same target and start
+    mh = hmc.MHSampler(tgt, hmc.Prior(eta0), q_start, seed=6, cut=cut)
+    mh.iteration = ex.iteration
+    mh.log_scale = np.log(np.sqrt(np.stack([np.diag(c) for c in cov]))) + np.log(2.38 / np.sqrt(6.0))
+    mh.warmup(50)
+    n0 = tgt.n_exact
+    d_mh, acc_mh, t_mh = mh.sample(draws)
+    ev_mh = tgt.n_exact - n0
+    s_mh = dg.summary(d_mh, hmc.NAMES)
+    ess_mh = min(v["bulk_ess"] for v in s_mh.values())
     s_ex, s_su = dg.summary(d_ex, hmc.NAMES), dg.summary(d_su, hmc.NAMES)
     ess_ex = min(v["bulk_ess"] for v in s_ex.values())
     ess_su = min(v["bulk_ess"] for v in s_su.values())
@@ -240,6 +250,8 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
             "surrogate": {"min_bulk_ess": ess_su, "seconds": t_su, "ess_per_s": ess_su / t_su,
                           "ess_per_s_incl_warmup_and_training": ess_su / (t_su + t_warm + t_train),
                           "accept": float(acc_su.mean()), "exact_evals": ev_su},
+            "univariate_mh": {"min_bulk_ess": ess_mh, "seconds": t_mh, "ess_per_s": ess_mh / t_mh,
+                              "accept": float(acc_mh.mean()), "exact_evals": ev_mh},
             "speedup_ess_per_s": (ess_su / t_su) / (ess_ex / t_ex),
             "warmup_s": t_warm, "train_s": t_train,
             "mean_diff_in_mcse_units": {k: float(v) for k, v in z.items()},

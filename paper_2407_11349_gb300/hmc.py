@@ -320,6 +320,66 @@ class Sampler:
         self.rng.bit_generator.state = st["rng"]
 
 
+class MHSampler:
+    """The paper's sampler (Sec. 2.2): univariate-update random-walk
+    Metropolis-Hastings on eta = log p, one coordinate at a time, after a
+    fresh location draw each iteration (cut scheme).  Each coordinate's
+    proposal scale adapts during warmup towards an acceptance rate of 0.44
+    (Robbins-Monro on its log).  Chains advance in lockstep: each univariate
+    update is one batched exact evaluation of all chains."""
+
+    def __init__(self, target, prior, eta_init, seed=0, cut=True):
+        self.target = target
+        self.prior = prior
+        self.q = np.array(eta_init, dtype=np.float64, copy=True)
+        self.C = self.q.shape[0]
+        self.cut = bool(cut)
+        self.rng = np.random.default_rng(seed)
+        self.log_scale = np.full((self.C, 6), np.log(0.01))
+        self.iteration = 0
+
+    def _logpost(self, eta, resample=False):
+        if resample:
+            ll, _ = self.target.resample_eval(self.iteration, eta)
+        else:
+            ll, _ = self.target.eval(eta)
+        return ll + self.prior(eta)[0]
+
+    def transition(self, adapt_rate=0.0):
+        """One iteration: new locations, then six univariate updates.
+        Returns the acceptance indicator array (C, 6)."""
+        self.iteration += 1
+        lp = self._logpost(self.q, resample=self.cut)
+        acc = np.zeros((self.C, 6))
+        for k in range(6):
+            prop = self.q.copy()
+            prop[:, k] += np.exp(self.log_scale[:, k]) * self.rng.standard_normal(self.C)
+            ok = np.all(np.abs(prop) <= ETA_MAX, axis=1)
+            lp_new = self._logpost(np.where(ok[:, None], prop, self.q))
+            log_a = np.where(ok & np.isfinite(lp_new), lp_new - lp, -np.inf)
+            take = np.log(self.rng.random(self.C)) < log_a
+            self.q[take] = prop[take]
+            lp = np.where(take, lp_new, lp)
+            acc[:, k] = take
+            if adapt_rate > 0:
+                a = np.exp(np.minimum(0.0, log_a))
+                self.log_scale[:, k] += adapt_rate * (a - 0.44)
+        return acc
+
+    def warmup(self, n):
+        for k in range(n):
+            self.transition(adapt_rate=1.0 / np.sqrt(k + 1.0))
+
+    def sample(self, n):
+        out = np.zeros((self.C, n, 6))
+        acc = np.zeros(n)
+        t0 = time.perf_counter()
+        for k in range(n):
+            acc[k] = self.transition().mean()
+            out[:, k] = self.q
+        return out, acc, time.perf_counter() - t0
+
+
 def save(path, sampler, mlp=None, train_X=None, train_Y=None):
     """Checkpoint the sampler (and the surrogate: weights + its training set,
     from which its standardisation is recomputed) to an .npz file."""

@@ -123,3 +123,18 @@ def test_checkpoint_resume_is_bit_identical(tmp_path):
     got = [b.transition().copy() for _ in range(15)]
     assert np.array_equal(np.stack(ref), np.stack(got))
     assert np.array_equal(ref_q, b.q)
+
+
+def test_univariate_mh_recovers_gaussian_posterior():
+    C = 4
+    tgt = GaussTarget(M, S, C)
+    mh = hmc.MHSampler(tgt, hmc.Prior(ETA0), np.tile(M, (C, 1)), seed=3)
+    mh.warmup(500)
+    draws, acc, _ = mh.sample(4000)
+    assert 0.25 < acc.mean() < 0.6
+    mean, var = posterior(M, S, ETA0)
+    summ = dg.summary(draws, hmc.NAMES)
+    for k, nm in enumerate(hmc.NAMES):
+        x = draws[:, :, k]
+        assert abs(x.mean() - mean[k]) < 4.5 * summ[nm]["mcse"], (nm, x.mean(), mean[k])
+        assert abs(x.var() / var[k] - 1) < 0.3
