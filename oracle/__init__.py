@@ -37,7 +37,7 @@ def _bind(L):
     for suf in ("f64", "ld"):
         f = getattr(L, "oracle_loglik_grad_" + suf)
         f.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D, ctypes.c_int64, ctypes.c_int64,
-                      _D, _D, ctypes.c_int]
+                      _D, _D, ctypes.c_int, ctypes.c_int]
         f.restype = ctypes.c_int
     L.oracle_max_threads_f64.restype = ctypes.c_int
     L.oracle_philox4x64_10.argtypes = [_U64, _U64, _U64]
@@ -57,14 +57,15 @@ def _f64(a):
 
 
 def loglik_grad(t, x, y, params, s=None, row_begin=0, row_end=None, rows=False,
-                threads=0, precision="f64", L=None):
+                threads=0, precision="f64", L=None, bg_time_only=False):
     """Eq. 4 log-likelihood and its gradient, as a plain double loop.
 
     ``params`` = (mu, tau_x, tau_t, theta, omega, h); ``s`` = per-event source
     bandwidth scale (None: s_j = 1).  Returns ``out7`` = [ell, d/dmu, d/dtau_x,
     d/dtau_t, d/dtheta, d/domega, d/dh]; with ``rows=True`` also the per-row
     array [m, 9] = (ell_i, six partials, log lambda_i, Lambda_i).
-    ``precision`` "ld" uses the long-double build.
+    ``precision`` "ld" uses the long-double build.  ``bg_time_only``: the
+    time-only background of eq. 2, mu phi1(dt; tau_t) / tau_x^2.
     """
     L = L or lib()
     t, x, y, s = _f64(t), _f64(x), _f64(y), _f64(s)
@@ -75,7 +76,7 @@ def loglik_grad(t, x, y, params, s=None, row_begin=0, row_end=None, rows=False,
     r9 = np.zeros((max(row_end - row_begin, 0), 9)) if rows else None
     f = getattr(L, "oracle_loglik_grad_" + precision)
     rc = f(n, _dp(t), _dp(x), _dp(y), _dp(s), _dp(p), row_begin, row_end, _dp(out), _dp(r9),
-           int(threads))
+           int(threads), 1 if bg_time_only else 0)
     if rc != 0:
         raise ValueError("oracle_loglik_grad: bad arguments")
     return (out, r9) if rows else out

@@ -16,6 +16,9 @@
  * Model (Sec. 2.1, eqs. 2-4, with the readings listed in the design notes):
  *   background pair term, for every j with t_j != t_i:
  *       B_ij = mu * phi2(r_ij; tau_x) * phi1(t_i - t_j; tau_t)
+ *   or, with the time-only background of eq. 2 (App. A writes its 1/A(X)
+ *   factor as tau_x^-2, so tau_x^2 stands for the domain area):
+ *       B_ij = mu * phi1(t_i - t_j; tau_t) / tau_x^2
  *   excitation pair term, for every j with t_j < t_i (eq. 3, the bandwidth
  *   belongs to the source event j):
  *       E_ij = theta * omega * exp(-omega (t_i - t_j)) * phi2(r_ij; h s_j)
@@ -86,7 +89,8 @@ static REAL phi1(REAL d, REAL sd) {
  *   [ell_i, d ell_i/d(mu, tau_x, tau_t, theta, omega, h), log lambda_i, Lambda_i].
  */
 static void one_row(int64_t n, const double* t, const double* x, const double* y,
-                    const double* s, const REAL p[6], REAL tN, int64_t i, REAL out9[9]) {
+                    const double* s, const REAL p[6], REAL tN, int64_t i, int bg_time_only,
+                    REAL out9[9]) {
     const REAL mu = p[0], tx = p[1], tt = p[2], th = p[3], om = p[4], h = p[5];
     REAL SB = 0, SBr = 0, SBt = 0, SE = 0, SEt = 0, SEq = 0;
     const REAL ti = t[i], xi = x[i], yi = y[i];
@@ -97,10 +101,16 @@ static void one_row(int64_t n, const double* t, const double* x, const double* y
         const REAL dx = xi - (REAL)x[j], dy = yi - (REAL)y[j];
         const REAL r2 = dx * dx + dy * dy;
         if (tj != ti) {                         /* background, indicator t_j != t_i */
-            const REAL b = phi2(r2, tx) * phi1(dt, tt);
-            SB += b;
-            SBr += b * r2;
-            SBt += b * dt * dt;
+            if (bg_time_only) {
+                const REAL b = phi1(dt, tt) / (tx * tx);
+                SB += b;                            /* no spatial moment: SBr stays 0 */
+                SBt += b * dt * dt;
+            } else {
+                const REAL b = phi2(r2, tx) * phi1(dt, tt);
+                SB += b;
+                SBr += b * r2;
+                SBt += b * dt * dt;
+            }
         }
         if (tj < ti) {                          /* excitation from earlier source j */
             const REAL sj = s ? (REAL)s[j] : (REAL)1;
@@ -151,12 +161,14 @@ static void one_row(int64_t n, const double* t, const double* x, const double* y
  *   rows9    optional [(row_end - row_begin) * 9] per-row values (see one_row)
  *   threads  OpenMP threads (<= 0: the OpenMP default); rows are summed in
  *            row order afterwards, so the result does not depend on it
+ *   bg_time_only  nonzero: the time-only background of eq. 2 (see above)
  * t_N is the largest time of all n events, also for a row window.
  * Returns 0, or -1 on bad arguments.
  */
 int SUF(oracle_loglik_grad)(int64_t n, const double* t, const double* x, const double* y,
                             const double* s, const double* params, int64_t row_begin,
-                            int64_t row_end, double* out7, double* rows9, int threads) {
+                            int64_t row_end, double* out7, double* rows9, int threads,
+                            int bg_time_only) {
     if (n < 1 || !t || !x || !y || !params || !out7) return -1;
     if (row_begin < 0 || row_end > n || row_begin > row_end) return -1;
     REAL p[6];
@@ -171,7 +183,8 @@ int SUF(oracle_loglik_grad)(int64_t n, const double* t, const double* x, const d
     if (threads <= 0) threads = omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 16) num_threads(threads)
 #endif
-    for (int64_t r = 0; r < m; ++r) one_row(n, t, x, y, s, p, tN, row_begin + r, rows + 9 * r);
+    for (int64_t r = 0; r < m; ++r)
+        one_row(n, t, x, y, s, p, tN, row_begin + r, bg_time_only, rows + 9 * r);
     REAL acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int64_t r = 0; r < m; ++r)
         for (int k = 0; k < 7; ++k) acc[k] += rows[9 * r + k];

@@ -12,7 +12,7 @@ import math
 
 import numpy as np
 from scipy import integrate
-from scipy.stats import expon, norm
+from scipy.stats import expon, norm, uniform
 
 import oracle
 
@@ -35,9 +35,11 @@ def small_events(n, seed, T=30.0, L=60.0, ties=False):
 # Independent formulations
 # ---------------------------------------------------------------------------
 
-def scipy_loglam(t, x, y, s, p):
+def scipy_loglam(t, x, y, s, p, bg_time_only=False):
     """log lambda_i from scipy.stats densities (product of 1-D normals for the
-    spherical 2-D Gaussian, expon for the temporal decay), masks as eq. 2-3."""
+    spherical 2-D Gaussian, expon for the temporal decay), masks as eq. 2-3.
+    bg_time_only: eq. 2's background, a uniform density over a domain of area
+    tau_x^2 times a normal density in time."""
     mu, tx, tt, th, om, h = p
     n = t.shape[0]
     s = np.ones(n) if s is None else s
@@ -45,7 +47,10 @@ def scipy_loglam(t, x, y, s, p):
     for i in range(n):
         dt, dx, dy = t[i] - t, x[i] - x, y[i] - y
         bg = (t != t[i])
-        b = norm.pdf(dx, scale=tx) * norm.pdf(dy, scale=tx) * norm.pdf(dt, scale=tt)
+        if bg_time_only:
+            b = norm.pdf(dt, scale=tt) * uniform.pdf(0.0, scale=tx * tx)
+        else:
+            b = norm.pdf(dx, scale=tx) * norm.pdf(dy, scale=tx) * norm.pdf(dt, scale=tt)
         ex = t < t[i]
         sd = h * s
         e = expon.pdf(dt, scale=1.0 / om) * norm.pdf(dx, scale=sd) * norm.pdf(dy, scale=sd)
@@ -140,6 +145,43 @@ def pin_scipy_general(L, n=60, seed=1, ties=False, model1=False, p=P0):
                 f"Lambda {e_La:.3g}, total {e_tot:.3g}")
 
 
+def pin_bg_time_scipy(L, n=60, seed=14, ties=True):
+    """Eq. 2's time-only background against the scipy formulation; Lambda is
+    the same as for the space-time background (both kernels have unit mass)."""
+    t, x, y, s = small_events(n, seed, ties=ties)
+    out, rows = oracle.loglik_grad(t, x, y, P0, s=s, rows=True, L=L, bg_time_only=True)
+    ll = scipy_loglam(t, x, y, s, P0, bg_time_only=True)
+    La = scipy_Lambda(t, P0)
+    e_ll = rel(rows[:, 7], ll, floor=1.0)
+    e_La = rel(rows[:, 8], La, floor=1e-3)
+    e_tot = abs(out[0] - (ll.sum() - La.sum())) / abs(out[0])
+    ok = e_ll < 1e-12 and e_La < 1e-12 and e_tot < 1e-12
+    return ok, f"time-only background vs scipy: log lambda {e_ll:.3g}, Lambda {e_La:.3g}, total {e_tot:.3g}"
+
+
+def pin_bg_time_theta0(L, n=70, seed=15):
+    """Time-only background with theta = 0: lambda_i = mu K_i / tau_x^2 with K_i
+    a sum over times only, so (a) ell and every partial derivative but d/d theta
+    do not depend on the locations at all,
+    (b) d ell/d tau_x = -2 m / tau_x and (c) d ell/d mu = m / mu - sum_i
+    [Phi((t_N - t_i)/tau_t) - Phi(-t_i/tau_t)], m = number of unclipped rows."""
+    t, x, y, s = small_events(n, seed, ties=True)
+    p = (0.5, 20.0, 7.0, 0.0, 0.2, 2.0)
+    a = oracle.loglik_grad(t, x, y, p, s=s, L=L, bg_time_only=True)
+    rng = np.random.default_rng(seed)
+    b = oracle.loglik_grad(t, rng.uniform(-1e3, 1e3, n), rng.uniform(-1e3, 1e3, n), p, s=s, L=L,
+                           bg_time_only=True)
+    keep = [0, 1, 2, 3, 5, 6]
+    e1 = rel(b[keep], a[keep], floor=1e-6 * abs(a[0]))
+    m = int(np.sum([np.any(t != ti) for ti in t]))
+    mu, tx, tt = p[0], p[1], p[2]
+    e2 = abs(a[2] - (-2.0 * m / tx)) / (2.0 * m / tx)
+    dmu = m / mu - (norm.cdf((t.max() - t) / tt) - norm.cdf(-t / tt)).sum()
+    e3 = abs(a[1] - dmu) / abs(dmu)
+    ok = e1 < 1e-13 and e2 < 1e-13 and e3 < 1e-12
+    return ok, f"time-only theta=0: location-free {e1:.3g}, d/dtau_x {e2:.3g}, d/dmu {e3:.3g}"
+
+
 def pin_quad_Lambda(L, n=40, seed=2):
     t, x, y, s = small_events(n, seed)
     p = P0
@@ -213,10 +255,10 @@ def pin_invariances(L, n=120, seed=6):
     return ok, f"rotation+translation {e1:.3g}, permutation {e2:.3g}, time shift vs closed form {e3:.3g}"
 
 
-def pin_finite_differences(L, n=150, seed=7, ties=False, p=P0):
+def pin_finite_differences(L, n=150, seed=7, ties=False, p=P0, bg_time_only=False):
     """Central differences in log-parameter space with one Richardson step."""
     t, x, y, s = small_events(n, seed, ties=ties)
-    g = oracle.loglik_grad(t, x, y, p, s=s, L=L)
+    g = oracle.loglik_grad(t, x, y, p, s=s, L=L, bg_time_only=bg_time_only)
     eta = np.log(np.asarray(p, float))
     worst = 0.0
     ok = True
@@ -227,7 +269,7 @@ def pin_finite_differences(L, n=150, seed=7, ties=False, p=P0):
         def f(e):
             q = np.exp(eta.copy())
             q[k] = math.exp(e)
-            return oracle.loglik_grad(t, x, y, q, s=s, L=L)[0]
+            return oracle.loglik_grad(t, x, y, q, s=s, L=L, bg_time_only=bg_time_only)[0]
 
         def D(hh):
             return (f(eta[k] + hh) - f(eta[k] - hh)) / (2 * hh)
@@ -237,7 +279,8 @@ def pin_finite_differences(L, n=150, seed=7, ties=False, p=P0):
         err = abs(fd - an) / (abs(an) + 1e-6 * abs(g[0]) + 1e-8)
         worst = max(worst, err)
         ok = ok and err < 1e-7
-    return ok, f"finite differences (n={n}, ties={ties}): worst rel {worst:.3g}"
+    return ok, (f"finite differences (n={n}, ties={ties}, time-only background {bg_time_only}): "
+                f"worst rel {worst:.3g}")
 
 
 def pin_long_double(L, n=100, seed=8):
@@ -265,4 +308,6 @@ ALL_PINS = [
     pin_finite_differences,
     lambda L: pin_finite_differences(L, n=90, seed=13, ties=True),
     pin_long_double, pin_row_window,
+    pin_bg_time_scipy, pin_bg_time_theta0,
+    lambda L: pin_finite_differences(L, n=90, seed=16, ties=True, bg_time_only=True),
 ]

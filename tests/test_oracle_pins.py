@@ -48,6 +48,11 @@ MUTATIONS = [
     ("time difference reversed", "const REAL dt = ti - tj;", "const REAL dt = tj - ti;"),
     ("t_N from the last input", "if (t[j] > tN) tN = t[j];", "tN = t[j];"),
     ("dropped tau_x factor 2", "- 2 * SB / tx", "- SB / tx"),
+    ("time-only background keeps the spatial Gaussian", "const REAL b = phi1(dt, tt) / (tx * tx);",
+     "const REAL b = phi2(r2, tx) * phi1(dt, tt);"),
+    ("time-only area factor not squared", "phi1(dt, tt) / (tx * tx)", "phi1(dt, tt) / tx"),
+    ("time-only background with a spatial moment", "SB += b;                            /*",
+     "SB += b; SBr += b * r2; /*"),
 ]
 
 
