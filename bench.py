@@ -47,7 +47,7 @@ def peaks():
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("sweep.cu", "common.cuh"):
+    for f in ("sweep_kernel.cuh", "sweep.cu", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2407_11349_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -358,7 +358,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2407_11349_gb300 import synth
-    from paper_2407_11349_gb300.hawkes import HAWKES_F32, HAWKES_SKIP_UNDERFLOW, Hawkes
+    from paper_2407_11349_gb300.hawkes import HAWKES_BG_TIME, HAWKES_F32, HAWKES_SKIP_UNDERFLOW, Hawkes
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -448,6 +448,23 @@ def main():
             "note": "tiles whose every pair term is an exact FP32 zero are skipped "
                     "(HAWKES_SKIP_UNDERFLOW); not the headline"}
 
+    # the same step with eq. 2's time-only background (a model option, not the headline)
+    bgt_ms = []
+    for k in range(args.steps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        hk.resample(2, chain, 700 + k)
+        hk.loglik_grad(p, HAWKES_F32 | HAWKES_BG_TIME)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            bgt_ms.append(e0.elapsed_time(e1))
+    bg_time = {"ms_per_step": sum(bgt_ms) / len(bgt_ms),
+               "pairs_per_s": pairs / (sum(bgt_ms) / len(bgt_ms) / 1000.0),
+               "note": "background mu phi1(dt; tau_t) / tau_x^2 (HAWKES_BG_TIME), same variant; "
+                       "a model option, not the headline"}
+
     # end to end through the C ABI from pinned host buffers, every step
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
            for k, v in (("t", ds.t), ("x", ds.x), ("y", ds.y), ("county", ds.county.astype(np.int32)),
@@ -493,6 +510,7 @@ def main():
                          "launch_ms": 1000 * sweep_avg_s},
             "clocks": clk.summary(),
             "skip_underflow": skip,
+            "bg_time": bg_time,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
         }

@@ -75,7 +75,18 @@ enum {
      * contribute no excitation.  The result is the same as without the flag
      * (the skipped terms are exact zeros); only the work shrinks.
      */
-    HAWKES_SKIP_UNDERFLOW = 4
+    HAWKES_SKIP_UNDERFLOW = 4,
+    /*
+     * The background exactly as eq. 2 prints it: a time-only Gaussian with a
+     * constant spatial density, mu phi1(t_i - t_j; tau_t) / A, where the
+     * kernel listing of App. A writes 1/A as tau_x^-2, so tau_x^2 plays the
+     * role of the domain area A.  Lambda_i is unchanged (the spatial factor
+     * has unit mass over the domain), d ell / d tau_x reduces to the -2/tau_x
+     * factor of the constant, and mu and tau_x enter only as mu / tau_x^2.
+     * Without this flag the background is the space-time Gaussian
+     * mu phi2(r; tau_x) phi1(dt; tau_t).  Combines with every other flag.
+     */
+    HAWKES_BG_TIME = 8
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -137,7 +148,8 @@ int hawkes_get_locations(hawkes_ctx* ctx, double* x, double* y);
  * of [0, n) gives the whole; every window uses all n events as sources and
  * the global t_N).  Pass row_begin = 0, row_end = n for the whole sum.
  *   params     host pointer
- *   flags      HAWKES_F32 or HAWKES_F64, | HAWKES_MODEL1 for s_j = 1
+ *   flags      HAWKES_F32 or HAWKES_F64, | HAWKES_MODEL1 for s_j = 1,
+ *              | HAWKES_SKIP_UNDERFLOW, | HAWKES_BG_TIME
  *   loglik     host pointer to one double (ell)
  *   grad       host pointer to six doubles, d ell / d (mu, tau_x, tau_t, theta, omega, h)
  * Synchronous: returns after the result is on the host.
@@ -227,6 +239,7 @@ int hawkes_tune(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags, in
  *   seeds[P], streams[P]  resample keys of each problem (Philox key as in
  *                      hawkes_resample_locations), or both NULL for no resample
  *   flags              HAWKES_F32, optionally | HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW
+ *                      | HAWKES_BG_TIME
  *   cuda_stream        stream for the batch's work, or NULL for its own
  */
 typedef struct hawkes_batch hawkes_batch;
@@ -367,8 +380,8 @@ int hawkes_check_bounded_wait(hawkes_ctx* ctx, double* seconds);
  *   n             1 <= n <= HAWKES_NOALLOC_MAX_N (65,536); larger n returns
  *                 HAWKES_ERR_TOO_LARGE
  *   d_params      device pointer to one hawkes_params
- *   flags         HAWKES_F32, optionally | HAWKES_MODEL1 (the FP64 path is
- *                 not offered here)
+ *   flags         HAWKES_F32, optionally | HAWKES_MODEL1 | HAWKES_BG_TIME (the
+ *                 FP64 path and tile skipping are not offered here)
  *   d_out         device pointer to 7 doubles: ell, then the six partials
  *   cuda_stream   cudaStream_t of the current device to queue the work on
  *                 (NULL: the legacy default stream)

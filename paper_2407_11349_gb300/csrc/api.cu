@@ -32,7 +32,7 @@ cudaError_t sweep_setup_attributes();
 int sweep_num_variants();
 int sweep_blocks_per_sm(int v);
 std::vector<int4> sweep_items(int64_t n, int v);
-cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end);
+cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt);
 }  // namespace hk
 
 using namespace hk;
@@ -165,17 +165,18 @@ int select_variant(hawkes_ctx* c, int v) {
 int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags, int64_t rb,
                    int64_t re, double* d_out, double* d_rows9) {
     const bool f64 = (flags & HAWKES_F64) != 0;
-    const int model1 = (flags & HAWKES_MODEL1) ? 1 : 0;
+    const int model = static_cast<int>(flags & (HAWKES_MODEL1 | HAWKES_BG_TIME));
+    const bool bgt = (flags & HAWKES_BG_TIME) != 0;
     const int skip = (!f64 && (flags & HAWKES_SKIP_UNDERFLOW)) ? 1 : 0;
     const int prep_grid = grid_for(c, c->npad);
     HK_TRY(timed(c, HAWKES_K_PREP, [&] {
-        k_prep<<<prep_grid, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->tb, d_params, model1,
+        k_prep<<<prep_grid, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->tb, d_params, model,
                                                   f64 ? 0 : 1, skip, c->n, c->npad, c->rec, c->acc,
                                                   c->cc, c->ctr, c->fix7);
     }));
     if (!f64) {
         const bool sym = (rb == 0 && re == c->n);
-        HK_TRY(timed(c, HAWKES_K_SWEEP, [&] { launch_sweep(c, sym, rb, re); }));
+        HK_TRY(timed(c, HAWKES_K_SWEEP, [&] { launch_sweep(c, sym, rb, re, bgt); }));
         HK_TRY(timed(c, HAWKES_K_FINAL, [&] {
             k_finalize<<<c->final_blocks, 256, 0, c->stream>>>(c->acc, c->t, c->cc, c->npad, rb, re, 1,
                                                                c->fixlist, c->ctr, c->partials,
@@ -183,7 +184,7 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
         }));
         HK_TRY(timed(c, HAWKES_K_ROWS64, [&] {
             k_rows64<<<c->sms, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc,
-                                                    model1, c->n, c->npad, 0, 0, 1, c->fixlist,
+                                                    model, c->n, c->npad, 0, 0, 1, c->fixlist,
                                                     c->ctr, c->acc, c->fix7, d_rows9);
         }));
     } else {
@@ -191,7 +192,7 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
         int g = static_cast<int>(count < static_cast<int64_t>(c->sms) * 16 ? count : c->sms * 16);
         if (g < 1) g = 1;
         HK_TRY(timed(c, HAWKES_K_ROWS64, [&] {
-            k_rows64<<<g, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model1,
+            k_rows64<<<g, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model,
                                                c->n, c->npad, rb, count, 0, c->fixlist, c->ctr,
                                                c->acc, c->fix7, d_rows9);
         }));
@@ -211,7 +212,7 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
 int sync_loglik(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int64_t rb, int64_t re,
                 double* out7, double* rows_host) {
     if (!params_ok(p)) return HAWKES_ERR_ARG;
-    if ((flags & ~7u) != 0) return HAWKES_ERR_ARG;
+    if ((flags & ~kFlagsAll) != 0) return HAWKES_ERR_ARG;
     HK_CUDA(cudaMemcpyAsync(c->params_dev, p, sizeof(hawkes_params), cudaMemcpyHostToDevice,
                             c->stream));
     double* d_rows9 = nullptr;
@@ -470,7 +471,7 @@ int hawkes_loglik_grad(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, in
 int hawkes_loglik_grad_async(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
                              double* d_out) {
     if (!c || !d_params || !d_out) return HAWKES_ERR_ARG;
-    if ((flags & ~7u) != 0) return HAWKES_ERR_ARG;
+    if ((flags & ~kFlagsAll) != 0) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
     return enqueue_loglik(c, d_params, flags, 0, c->n, d_out, nullptr);
@@ -517,7 +518,7 @@ int hawkes_tune(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int reps,
                 double* ms) {
     if (!c || !p || reps < 1) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
-    if (!params_ok(p) || (flags & ~(uint32_t)(HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW)) != 0)
+    if (!params_ok(p) || (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64))) != 0)
         return HAWKES_ERR_ARG;
     DeviceGuard g(c->device);
     const bool prof = c->prof;

@@ -27,7 +27,7 @@ int sweep_num_variants();
 int sweep_blocks_per_sm(int v);
 std::vector<int4> sweep_items_batch(const std::vector<int64_t>& ns, int v, int chunk, int order);
 cudaError_t launch_sweep_batch(cudaStream_t st, int variant, int grid, const ProbDesc* probs,
-                               const int4* items, int nitems, int* ctr);
+                               const int4* items, int nitems, int* ctr, bool bgt);
 
 __global__ void k_set_u64(uint64_t* dst, uint64_t v) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
@@ -120,7 +120,8 @@ int build_items(hawkes_batch* b, int variant, int chunk, int order) {
 // from b->d_iter by the resample kernels.
 int enqueue(hawkes_batch* b, const hawkes_params* d_params, double* d_out, bool time_sweep) {
     cudaStream_t st = b->stream;
-    const int model1 = (b->flags & HAWKES_MODEL1) ? 1 : 0;
+    const int model = static_cast<int>(b->flags & (HAWKES_MODEL1 | HAWKES_BG_TIME));
+    const bool bgt = (b->flags & HAWKES_BG_TIME) != 0;
     const int skip = (b->flags & HAWKES_SKIP_UNDERFLOW) ? 1 : 0;
     const int P = static_cast<int>(b->probs.size());
     for (int p = 0; p < P; ++p) {
@@ -130,18 +131,19 @@ int enqueue(hawkes_batch* b, const hawkes_params* d_params, double* d_out, bool 
         if (b->resample)
             k_resample<<<g, 256, 0, st>>>(c->county, c->n, c->tri_xy, c->tri_cum, c->cfirst, c->clast,
                                           b->seeds[p], b->streams[p], 0, b->d_iter, c->x, c->y);
-        k_prep<<<g, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->tb, d_params + p, model1, 1, skip,
+        k_prep<<<g, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->tb, d_params + p, model, 1, skip,
                                   c->n, c->npad, c->rec, c->acc, c->cc, c->ctr, c->fix7);
     }
     HB_CUDA(cudaMemsetAsync(b->d_ctr + CT_WORK, 0, sizeof(int), st));
     if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[0], st));
-    HB_CUDA(launch_sweep_batch(st, b->variant, b->grid, b->d_probs, b->d_items, b->nitems, b->d_ctr));
+    HB_CUDA(launch_sweep_batch(st, b->variant, b->grid, b->d_probs, b->d_items, b->nitems, b->d_ctr,
+                               bgt));
     if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[1], st));
     for (int p = 0; p < P; ++p) {
         hawkes_ctx* c = b->probs[p];
         k_finalize<<<c->final_blocks, 256, 0, st>>>(c->acc, c->t, c->cc, c->npad, 0, c->n, 1,
                                                     c->fixlist, c->ctr, c->partials, nullptr);
-        k_rows64<<<b->sms, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model1, c->n,
+        k_rows64<<<b->sms, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model, c->n,
                                          c->npad, 0, 0, 1, c->fixlist, c->ctr, c->acc, c->fix7,
                                          nullptr);
         k_reduce<<<1, 256, 0, st>>>(c->partials, c->final_blocks, c->fix7, c->cc, d_out + 7 * p,
@@ -178,7 +180,7 @@ int hawkes_batch_create(hawkes_batch** out, hawkes_ctx* const* problems, int32_t
     if (!out) return HAWKES_ERR_ARG;
     *out = nullptr;
     if (!problems || n_problems < 1 ||
-        (flags & ~static_cast<uint32_t>(HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW)) != 0 ||
+        (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64))) != 0 ||
         (seeds == nullptr) != (streams == nullptr))
         return HAWKES_ERR_ARG;
     const int dev = problems[0] ? problems[0]->device : -1;

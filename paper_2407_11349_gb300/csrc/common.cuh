@@ -19,6 +19,9 @@ namespace hk {
 //   relative to the first event of their block of TB = TC events.  Event
 //   arrays are padded to a multiple of NPAD_MULT (the largest row tile).
 // ---------------------------------------------------------------------------
+// Every flag bit the log-likelihood calls accept.
+constexpr uint32_t kFlagsAll = HAWKES_F64 | HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW | HAWKES_BG_TIME;
+
 constexpr int WARPS = 8;
 constexpr int THREADS = WARPS * 32;
 constexpr int TC = 256;

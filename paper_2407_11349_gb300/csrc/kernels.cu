@@ -75,7 +75,7 @@ struct Consts {
     bool valid;
 };
 
-__device__ __forceinline__ Consts make_consts(const hawkes_params* P) {
+__device__ __forceinline__ Consts make_consts(const hawkes_params* P, bool bg_time) {
     Consts k;
     k.mu = P->mu; k.tx = P->tau_x; k.tt = P->tau_t; k.th = P->theta; k.om = P->omega; k.h = P->h;
     k.valid = isfinite(k.mu) && isfinite(k.tx) && isfinite(k.tt) && isfinite(k.th) &&
@@ -89,20 +89,25 @@ __device__ __forceinline__ Consts make_consts(const hawkes_params* P) {
     k.st = 1.0 / at;
     k.set = 1.0 / k.kt;
     k.seq = 2.0 * k.h * k.h / LOG2E;
-    k.cB = 1.0 / (TWO_PI * sqrt(TWO_PI) * k.tx * k.tx * k.tt);
+    // Space-time background phi2(r; tau_x) phi1(dt; tau_t), or the time-only
+    // background phi1(dt; tau_t) / tau_x^2 (eq. 2, tau_x^2 read as the area).
+    k.cB = bg_time ? 1.0 / (sqrt(TWO_PI) * k.tx * k.tx * k.tt)
+                   : 1.0 / (TWO_PI * sqrt(TWO_PI) * k.tx * k.tx * k.tt);
     k.cE = k.om / (TWO_PI * k.h * k.h);
     return k;
 }
 
 // Zero the accumulators, reset the counters and (FP32 path) stage the event table.
+// model: the HAWKES_MODEL1 and HAWKES_BG_TIME bits of the call's flags.
 // skip: evaluate only tiles whose terms can be nonzero in FP32 (see CC_SKIPDT).
 __global__ void k_prep(const double* __restrict__ t, const double* __restrict__ x,
                        const double* __restrict__ y, const double* __restrict__ s,
-                       const double* __restrict__ tb, const hawkes_params* P, int model1,
+                       const double* __restrict__ tb, const hawkes_params* P, int model,
                        int stage, int skip, int64_t n, int64_t npad, Rec* __restrict__ rec,
                        double* __restrict__ acc, double* __restrict__ cc, int* ctr,
                        double* fix7) {
-    const Consts k = make_consts(P);
+    const bool model1 = (model & HAWKES_MODEL1) != 0;
+    const Consts k = make_consts(P, (model & HAWKES_BG_TIME) != 0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         cc[CC_KX] = k.kx; cc[CC_KT] = k.kt; cc[CC_OMT] = k.omt;
         cc[CC_SR] = k.sr; cc[CC_ST] = k.st; cc[CC_SET] = k.set; cc[CC_SEQ] = k.seq;
@@ -263,12 +268,15 @@ __global__ void k_finalize(const double* __restrict__ acc, const double* __restr
 __global__ void k_rows64(const double* __restrict__ t, const double* __restrict__ x,
                          const double* __restrict__ y, const double* __restrict__ s,
                          const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
-                         const double* __restrict__ cc, int model1, int64_t n, int64_t npad,
+                         const double* __restrict__ cc, int model, int64_t n, int64_t npad,
                          int64_t row_begin, int64_t count, int mode, const int* fixlist, int* ctr,
                          double* acc, double* fix7, double* rows9) {
     if (cc[CC_VALID] == 0.0) return;
+    const bool model1 = (model & HAWKES_MODEL1) != 0;
     const double tx = cc[CC_TX], tt = cc[CC_TT], om = cc[CC_OM], h = cc[CC_H];
-    const double ix2 = 1.0 / (2.0 * tx * tx), it2 = 1.0 / (2.0 * tt * tt), ih2 = 1.0 / (2.0 * h * h);
+    // Time-only background: no spatial factor in B and no r^2 moment.
+    const double ix2 = (model & HAWKES_BG_TIME) ? 0.0 : 1.0 / (2.0 * tx * tx);
+    const double it2 = 1.0 / (2.0 * tt * tt), ih2 = 1.0 / (2.0 * h * h);
     const int64_t total = mode ? static_cast<int64_t>(ctr[CT_FIX]) : count;
     for (int64_t k = blockIdx.x; k < total; k += gridDim.x) {
         const int64_t i = mode ? fixlist[k] : row_begin + k;
@@ -281,7 +289,7 @@ __global__ void k_rows64(const double* __restrict__ t, const double* __restrict_
             if (j < li || j >= hj) {
                 const double b = exp(-r2 * ix2 - dt * dt * it2);
                 v[0] += b;
-                v[1] += b * r2;
+                v[1] += ix2 != 0.0 ? b * r2 : 0.0;
                 v[2] += b * dt * dt;
             }
             if (j < li) {

@@ -36,7 +36,7 @@ __global__ void k_reduce(const double*, int, const double*, const double*, doubl
 cudaError_t sweep_setup_attributes();
 int sweep_blocks_per_sm(int v);
 int sweep_variant_rows(int v);
-cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end);
+cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt);
 }  // namespace hk
 
 using namespace hk;
@@ -186,7 +186,8 @@ extern "C" int hawkes_loglik_grad_noalloc(const double* d_t, const double* d_x, 
                                           const hawkes_params* d_params, uint32_t flags,
                                           double* d_out, void* cuda_stream) {
     if (!d_t || !d_x || !d_y || !d_params || !d_out) return HAWKES_ERR_ARG;
-    if ((flags & ~static_cast<uint32_t>(HAWKES_MODEL1)) != 0) return HAWKES_ERR_ARG;  // FP32 only
+    if ((flags & ~static_cast<uint32_t>(HAWKES_MODEL1 | HAWKES_BG_TIME)) != 0)
+        return HAWKES_ERR_ARG;  // FP32 only
     if (n < 1) return HAWKES_ERR_ARG;
     if (n > kMaxN) return HAWKES_ERR_TOO_LARGE;
     int dev = -1;
@@ -232,7 +233,7 @@ extern "C" int hawkes_loglik_grad_noalloc(const double* d_t, const double* d_x, 
     c.variant_bpsm = d->bpsm;
     c.final_blocks = 2 * d->sms < kMaxFinalBlocks ? 2 * d->sms : kMaxFinalBlocks;
     if (c.nitems > kMaxItems) return HAWKES_ERR_TOO_LARGE;
-    const int model1 = (flags & HAWKES_MODEL1) ? 1 : 0;
+    const int model = static_cast<int>(flags & (HAWKES_MODEL1 | HAWKES_BG_TIME));
     int grid = static_cast<int>((npad + 255) / 256);
     if (grid > 8 * c.sms) grid = 8 * c.sms;
 
@@ -241,12 +242,12 @@ extern "C" int hawkes_loglik_grad_noalloc(const double* d_t, const double* d_x, 
     k_na_setup<<<grid, 256, 0, st>>>(d_t, d_x, d_y, d_s, n, npad, c.t, c.x, c.y, c.s, c.lo, c.hi,
                                      c.tb, c.ctr);
     k_na_items<<<1, 32, 0, st>>>(n, tr, c.items);
-    k_prep<<<grid, 256, 0, st>>>(c.t, c.x, c.y, c.s, c.tb, d_params, model1, 1, 0, n, npad, c.rec,
+    k_prep<<<grid, 256, 0, st>>>(c.t, c.x, c.y, c.s, c.tb, d_params, model, 1, 0, n, npad, c.rec,
                                  c.acc, c.cc, c.ctr, c.fix7);
-    if (launch_sweep(&c, true, 0, n) != cudaSuccess) return HAWKES_ERR_CUDA;
+    if (launch_sweep(&c, true, 0, n, (flags & HAWKES_BG_TIME) != 0) != cudaSuccess) return HAWKES_ERR_CUDA;
     k_finalize<<<c.final_blocks, 256, 0, st>>>(c.acc, c.t, c.cc, npad, 0, n, 1, c.fixlist, c.ctr,
                                                c.partials, nullptr);
-    k_rows64<<<c.sms, 256, 0, st>>>(c.t, c.x, c.y, c.s, c.lo, c.hi, c.cc, model1, n, npad, 0, 0, 1,
+    k_rows64<<<c.sms, 256, 0, st>>>(c.t, c.x, c.y, c.s, c.lo, c.hi, c.cc, model, n, npad, 0, 0, 1,
                                     c.fixlist, c.ctr, c.acc, c.fix7, nullptr);
     k_reduce<<<1, 256, 0, st>>>(c.partials, c.final_blocks, c.fix7, c.cc, d_out, c.ctr);
     k_na_nan_on_error<<<1, 32, 0, st>>>(c.ctr, d_out);

@@ -23,6 +23,7 @@ HAWKES_F64 = 1
 HAWKES_MODEL2 = 0
 HAWKES_MODEL1 = 2
 HAWKES_SKIP_UNDERFLOW = 4
+HAWKES_BG_TIME = 8
 KERNEL_CLASSES = ("prep", "sweep", "rows64", "final", "reduce", "resample", "other")
 
 

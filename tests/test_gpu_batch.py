@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2407_11349_gb300 import synth
-from paper_2407_11349_gb300.hawkes import Batch, Hawkes, HAWKES_F32, HawkesError
+from paper_2407_11349_gb300.hawkes import Batch, Hawkes, HAWKES_BG_TIME, HAWKES_F32, HawkesError
 
 pytestmark = pytest.mark.gpu
 
@@ -38,11 +38,11 @@ def problems():
         h.close()
 
 
-def _sequential(hks, params, seeds, streams, it):
+def _sequential(hks, params, seeds, streams, it, flags=HAWKES_F32):
     out = []
     for h, p, sd, st in zip(hks, params, seeds, streams):
         h.resample(sd, st, it)
-        ref, rows = h.loglik_rows(p, HAWKES_F32)
+        ref, rows = h.loglik_rows(p, flags)
         out.append((ref, rows))
     return out
 
@@ -110,5 +110,27 @@ def test_batch_reports_invalid_problem(problems):
             b.wait()
         got = dout.cpu().numpy()
         assert np.all(np.isnan(got[2])) and np.all(np.isfinite(np.delete(got, 2, axis=0)))
+    finally:
+        b.close()
+
+
+def test_batch_time_only_background(problems):
+    """The batch with eq. 2's time-only background against sequential calls
+    with the same flag."""
+    torch, dss, params, hks, seeds, streams = problems
+    P = len(dss)
+    fl = HAWKES_F32 | HAWKES_BG_TIME
+    dp = torch.tensor(params, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+    b = Batch(hks, seeds, streams, fl)
+    try:
+        b.capture(dp.data_ptr(), dout.data_ptr())
+        torch.cuda.synchronize()
+        b.run(dp.data_ptr(), 9, dout.data_ptr())
+        b.wait()
+        got = dout.cpu().numpy()
+        ref = _sequential(hks, params, seeds, streams, 9, fl)
+        for p in range(P):
+            _close(got[p], *ref[p], f"time-only background problem {p}")
     finally:
         b.close()

@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 from paper_2407_11349_gb300 import synth
-from paper_2407_11349_gb300.hawkes import (HAWKES_F32, HAWKES_F64, HAWKES_MODEL1,
+from paper_2407_11349_gb300.hawkes import (HAWKES_BG_TIME, HAWKES_F32, HAWKES_F64, HAWKES_MODEL1,
                                            HAWKES_SKIP_UNDERFLOW, Hawkes, HawkesError)
 
 pytestmark = pytest.mark.gpu
@@ -38,9 +38,10 @@ def small_grid(n, seed=0, T=100.0):
     return synth.grid_dataset(n, T, 20, 20, seed=seed)
 
 
-def oracle_rows(ds, p=P0, model1=False):
+def oracle_rows(ds, p=P0, model1=False, bg_time=False, row_begin=0, row_end=None):
     s = None if model1 else ds.s
-    return oracle.loglik_grad(ds.t, ds.x, ds.y, p, s=s, rows=True)
+    return oracle.loglik_grad(ds.t, ds.x, ds.y, p, s=s, rows=True, bg_time_only=bg_time,
+                              row_begin=row_begin, row_end=row_end)
 
 
 def assert_close(got_ll, got_g, ref, ref_rows, tol_ll, tol_g, what=""):
@@ -277,3 +278,50 @@ def test_c3_full_size_sampled(hk):
         ll, g = hk.loglik_grad(P0, HAWKES_F32, a, b)
         tot += np.concatenate([[ll], g])
     assert_close(tot[0], tot[1:], out32, rows32, TOL_LL32, TOL_G32, "c3 shards")
+
+
+# ---------------------------------------------------------------------------
+# Eq. 2's time-only background (HAWKES_BG_TIME)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,ties,model1", [(1, False, False), (257, False, False),
+                                           (2049, False, True), (3000, True, False),
+                                           (5000, False, False)])
+def test_bg_time_matches_oracle(hk, n, ties, model1):
+    ds = small_grid(n, seed=40 + n)
+    if ties:
+        ds = synth.integer_day_times(ds)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle_rows(ds, model1=model1, bg_time=True)
+    fl = HAWKES_BG_TIME | (HAWKES_MODEL1 if model1 else 0)
+    ll, g = hk.loglik_grad(P0, HAWKES_F64 | fl)
+    assert_close(ll, g, ref, rows, TOL_F64, TOL_F64, f"bg_time n={n} f64")
+    ll, g = hk.loglik_grad(P0, HAWKES_F32 | fl)
+    assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, f"bg_time n={n} f32")
+    if n > 1:  # the background really changed
+        other = oracle_rows(ds, model1=model1)[0]
+        assert abs(other[0] - ref[0]) > 1e-3 * abs(ref[0])
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_bg_time_variants_and_windows(hk, variant):
+    ds = small_grid(6000, seed=41)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle_rows(ds, bg_time=True)
+    hk.set_variant(variant)
+    try:
+        ll, g = hk.loglik_grad(P0, HAWKES_F32 | HAWKES_BG_TIME)
+        assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, f"bg_time variant {variant}")
+        wref, _ = oracle_rows(ds, bg_time=True, row_begin=1000, row_end=4500)
+        ll, g = hk.loglik_grad(P0, HAWKES_F32 | HAWKES_BG_TIME, 1000, 4500)
+        assert_close(ll, g, wref, rows[1000:4500], TOL_LL32, TOL_G32, f"bg_time variant {variant} window")
+    finally:
+        hk.set_variant(0)
+
+
+def test_bg_time_with_underflow_skip(hk):
+    ds = synth.integer_day_times(synth.grid_dataset(6000, 1200.0, 20, 20, seed=42))
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle_rows(ds, bg_time=True)
+    ll, g = hk.loglik_grad(P0, HAWKES_F32 | HAWKES_BG_TIME | HAWKES_SKIP_UNDERFLOW)
+    assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, "bg_time + skip")

@@ -19,8 +19,9 @@ import numpy as np
 import pytest
 
 from paper_2407_11349_gb300 import synth
-from paper_2407_11349_gb300.hawkes import (HAWKES_F32, HAWKES_MODEL1, HAWKES_NOALLOC_MAX_N,
-                                           Hawkes, HawkesError, hawkes_loglik_grad_noalloc)
+from paper_2407_11349_gb300.hawkes import (HAWKES_BG_TIME, HAWKES_F32, HAWKES_MODEL1,
+                                           HAWKES_NOALLOC_MAX_N, Hawkes, HawkesError,
+                                           hawkes_loglik_grad_noalloc)
 
 pytestmark = pytest.mark.gpu
 
@@ -43,6 +44,7 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
     cases = [
         (synth.grid_dataset(40_000, 400.0, 40, 40, seed=21), HAWKES_F32),
         (synth.grid_dataset(5_000, 100.0, 20, 20, seed=22), HAWKES_F32 | HAWKES_MODEL1),
+        (synth.grid_dataset(3_000, 100.0, 20, 20, seed=23), HAWKES_F32 | HAWKES_BG_TIME),
     ]
     hk = Hawkes(0)
     dev = torch.device("cuda", 0)
