@@ -61,11 +61,38 @@ struct Rows {
 //   COL    also accumulate the background into the source columns
 //   BGT    time-only background (eq. 2): B' = exp(-dt^2/2tau_t^2), no SBr
 // rlo/rhi: shared-memory lo/hi of the lane's rows (masked tiles only).
+// racc: the thread's FP32 row accumulators in shared memory (see fold_rows).
+//
+// Summation order.  FP32 running sums of many similar terms (integer-day
+// times make whole runs of terms identical) drift by a rounding bias that
+// grows with the length of the chain, so every chain here is kept short:
+// a row's register sums cover one 32-column chunk before they are folded
+// into racc, and a column's sum takes each step's 2 RP rows as one partial.
+__device__ __forceinline__ void fold2(float4* q, float2 a, float2 b) {
+    const float4 v = *q;
+    const float2 lo = add2(f2(v.x, v.y), a), hi = add2(f2(v.z, v.w), b);
+    *q = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// racc layout per thread (stride THREADS float4): for each row pair p,
+// (SB, SBr), (SBt, SE), (SEt, SEq), each a float2 over the pair's two rows.
+template <int RP>
+__device__ __forceinline__ void fold_rows(Rows<RP>& rr, float4* __restrict__ racc) {
+#pragma unroll
+    for (int p = 0; p < RP; ++p) {
+        fold2(racc + (3 * p + 0) * THREADS, rr.sB[p], rr.sBr[p]);
+        fold2(racc + (3 * p + 1) * THREADS, rr.sBt[p], rr.sE[p]);
+        fold2(racc + (3 * p + 2) * THREADS, rr.sEt[p], rr.sEq[p]);
+        rr.sB[p] = rr.sBr[p] = rr.sBt[p] = rr.sE[p] = rr.sEt[p] = rr.sEq[p] = f2(0.f, 0.f);
+    }
+}
+
 template <int RP, int UNROLL, int MASK, bool EXC, bool COL, bool BGT>
 __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j0, int lane,
                                           Rows<RP>& rr, float2 nomt,
                                           const int* __restrict__ rlo,
-                                          const int* __restrict__ rhi, float* __restrict__ colacc) {
+                                          const int* __restrict__ rhi, float* __restrict__ colacc,
+                                          float4* __restrict__ racc) {
 #pragma unroll 1
     for (int ch = 0; ch < TC / 32; ++ch) {
         float2 cB = f2(0.f, 0.f), cBr = f2(0.f, 0.f), cBt = f2(0.f, 0.f);
@@ -81,6 +108,7 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
             const float2 nYL = f2(q2.x, q2.y), NB = f2(q2.z, q2.w);
             const float2 CE = f2(q3.x, q3.y);
             const int j = j0 + c;
+            float2 pB, pBr, pBt;  // this step's column partial over the lane's rows
 #pragma unroll
             for (int p = 0; p < RP; ++p) {
                 const float2 dt = add2(rr.tp[p], nT);
@@ -104,9 +132,15 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
                 if (!BGT) rr.sBr[p] = fma2(B, r2, rr.sBr[p]);
                 rr.sBt[p] = fma2(B, dt2, rr.sBt[p]);
                 if (COL) {
-                    cB = add2(cB, B);
-                    if (!BGT) cBr = fma2(B, r2, cBr);
-                    cBt = fma2(B, dt2, cBt);
+                    if (p == 0) {
+                        pB = B;
+                        if (!BGT) pBr = mul2(B, r2);
+                        pBt = mul2(B, dt2);
+                    } else {
+                        pB = add2(pB, B);
+                        if (!BGT) pBr = fma2(B, r2, pBr);
+                        pBt = fma2(B, dt2, pBt);
+                    }
                 }
                 if (EXC) {
                     const float2 nv = mul2(NB, r2);                  // -beta r~^2
@@ -122,6 +156,9 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
                 }
             }
             if (COL) {
+                cB = add2(cB, pB);
+                if (!BGT) cBr = add2(cBr, pBr);
+                cBt = add2(cBt, pBt);
                 const int src = (lane + 1) & 31;
                 cB.x = __shfl_sync(0xffffffffu, cB.x, src);
                 cB.y = __shfl_sync(0xffffffffu, cB.y, src);
@@ -138,6 +175,7 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
             if (!BGT) atomicAdd(colacc + 1 * TC + ch * 32 + lane, cBr.x + cBr.y);
             atomicAdd(colacc + 2 * TC + ch * 32 + lane, cBt.x + cBt.y);
         }
+        fold_rows<RP>(rr, racc);
     }
 }
 
@@ -150,7 +188,8 @@ struct Geo {
     static constexpr size_t SMEM_TILES = 2 * TC * sizeof(Rec);
     static constexpr size_t SMEM_COLACC = 2 * 3 * TC * sizeof(float);
     static constexpr size_t SMEM_LOHI = 2 * THREADS * R * sizeof(int);
-    static constexpr size_t SMEM = SMEM_TILES + SMEM_COLACC + SMEM_LOHI;
+    static constexpr size_t SMEM_RACC = 3 * RP * THREADS * sizeof(float4);
+    static constexpr size_t SMEM = SMEM_TILES + SMEM_COLACC + SMEM_LOHI + SMEM_RACC;
 };
 
 enum { MODE_WIN = 0, MODE_SYM = 1, MODE_BATCH = 2 };
@@ -175,6 +214,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
     float* colacc = reinterpret_cast<float*>(smem + G::SMEM_TILES);
     int* slo = reinterpret_cast<int*>(smem + G::SMEM_TILES + G::SMEM_COLACC);
     int* shi = slo + THREADS * R;
+    float4* racc = reinterpret_cast<float4*>(smem + G::SMEM_TILES + G::SMEM_COLACC + G::SMEM_LOHI) +
+                   threadIdx.x;
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ int s_item, s_abort;
     // The current item's problem.  In batch mode it is re-read from shared
@@ -267,6 +308,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
             rr.yh[p] = f2(-b0.z, -b1.z);
             rr.yl[p] = f2(-c0.x, -c1.x);
             rr.sB[p] = rr.sBr[p] = rr.sBt[p] = rr.sE[p] = rr.sEt[p] = rr.sEq[p] = f2(0.f, 0.f);
+            for (int q = 0; q < 3; ++q) racc[(3 * p + q) * THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
             mylo[2 * p] = plo[i0];
             mylo[2 * p + 1] = plo[i1];
             myhi[2 * p] = phi[i0];
@@ -314,17 +356,17 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 if (SYM) {
                     if (j0 < r0 + G::WROWS) {
                         if (j0 + TC > lo_first)
-                            tile_pass<RP, UNROLL, M_LOWER, true, true, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                            tile_pass<RP, UNROLL, M_LOWER, true, true, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                         else
-                            tile_pass<RP, UNROLL, M_NONE, true, true, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                            tile_pass<RP, UNROLL, M_NONE, true, true, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                     }
                 } else {
                     if (j0 + TC <= lo_first)
-                        tile_pass<RP, UNROLL, M_NONE, true, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                        tile_pass<RP, UNROLL, M_NONE, true, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                     else if (j0 >= hi_last)
-                        tile_pass<RP, UNROLL, M_NONE, false, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                        tile_pass<RP, UNROLL, M_NONE, false, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                     else
-                        tile_pass<RP, UNROLL, M_TWO, true, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca);
+                        tile_pass<RP, UNROLL, M_TWO, true, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                 }
             }
             __syncthreads();
@@ -362,12 +404,13 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 for (int h = 0; h < 2; ++h) {
                     const int64_t i = r0 + lane + 64 * p + 32 * h;
                     if (i >= n || (!SYM && (i < row_begin || i >= row_end))) continue;
-                    const float vB = h ? rr.sB[p].y : rr.sB[p].x;
-                    const float vBr = h ? rr.sBr[p].y : rr.sBr[p].x;
-                    const float vBt = h ? rr.sBt[p].y : rr.sBt[p].x;
-                    const float vE = h ? rr.sE[p].y : rr.sE[p].x;
-                    const float vEt = h ? rr.sEt[p].y : rr.sEt[p].x;
-                    const float vEq = h ? rr.sEq[p].y : rr.sEq[p].x;
+                    // racc holds (SB, SBr), (SBt, SE), (SEt, SEq) of rows (x, y)
+                    const float4 a = racc[(3 * p + 0) * THREADS];
+                    const float4 b = racc[(3 * p + 1) * THREADS];
+                    const float4 e = racc[(3 * p + 2) * THREADS];
+                    const float vB = h ? a.y : a.x, vBr = h ? a.w : a.z;
+                    const float vBt = h ? b.y : b.x, vE = h ? b.w : b.z;
+                    const float vEt = h ? e.y : e.x, vEq = h ? e.w : e.z;
                     if (vB != 0.f || vBr != 0.f || vBt != 0.f) {
                         atomicAdd(acc + 0 * npad + i, static_cast<double>(vB));
                         atomicAdd(acc + 1 * npad + i, static_cast<double>(vBr) * sr);
