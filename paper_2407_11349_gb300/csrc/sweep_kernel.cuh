@@ -61,13 +61,20 @@ struct Rows {
 //   COL    also accumulate the background into the source columns
 //   BGT    time-only background (eq. 2): B' = exp(-dt^2/2tau_t^2), no SBr
 // rlo/rhi: shared-memory lo/hi of the lane's rows (masked tiles only).
-// racc: the thread's FP32 row accumulators in shared memory (see fold_rows).
+// racc: the thread's FP32 row accumulators in shared memory (see fold_rows;
+// time-only background only).
 //
-// Summation order.  FP32 running sums of many similar terms (integer-day
-// times make whole runs of terms identical) drift by a rounding bias that
-// grows with the length of the chain, so every chain here is kept short:
-// a row's register sums cover one 32-column chunk before they are folded
-// into racc, and a column's sum takes each step's 2 RP rows as one partial.
+// Summation order.  An FP32 running sum of many equal terms drifts by a
+// rounding bias that grows with the length of the chain.  With the time-only
+// background every pair at the same time gap has the same B', and
+// integer-day times make whole runs of them, so the BGT kernels keep every
+// chain short: a row's register sums cover one 32-column chunk before they
+// are folded into racc, and a column's sum takes each step's 2 RP rows as one
+// partial (at N = 100,000 on integer days this takes the d/dtau_t error from
+// 8e-5 to 7e-7 of its value).  With the space-time background the spatial
+// factor makes the terms differ and the plain chains stay within 2e-7 of the
+// FP64 path up to N = 1,000,000 on integer days, so those kernels keep the
+// cheaper order.
 __device__ __forceinline__ void fold2(float4* q, float2 a, float2 b) {
     const float4 v = *q;
     const float2 lo = add2(f2(v.x, v.y), a), hi = add2(f2(v.z, v.w), b);
@@ -108,7 +115,7 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
             const float2 nYL = f2(q2.x, q2.y), NB = f2(q2.z, q2.w);
             const float2 CE = f2(q3.x, q3.y);
             const int j = j0 + c;
-            float2 pB, pBr, pBt;  // this step's column partial over the lane's rows
+            float2 pB, pBt;  // BGT: this step's column partial over the lane's rows
 #pragma unroll
             for (int p = 0; p < RP; ++p) {
                 const float2 dt = add2(rr.tp[p], nT);
@@ -131,16 +138,14 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
                 rr.sB[p] = add2(rr.sB[p], B);
                 if (!BGT) rr.sBr[p] = fma2(B, r2, rr.sBr[p]);
                 rr.sBt[p] = fma2(B, dt2, rr.sBt[p]);
-                if (COL) {
-                    if (p == 0) {
-                        pB = B;
-                        if (!BGT) pBr = mul2(B, r2);
-                        pBt = mul2(B, dt2);
-                    } else {
-                        pB = add2(pB, B);
-                        if (!BGT) pBr = fma2(B, r2, pBr);
-                        pBt = fma2(B, dt2, pBt);
-                    }
+                if (COL && !BGT) {
+                    cB = add2(cB, B);
+                    cBr = fma2(B, r2, cBr);
+                    cBt = fma2(B, dt2, cBt);
+                }
+                if (COL && BGT) {  // per-step partial (no SBr moment here)
+                    pB = (p == 0) ? B : add2(pB, B);
+                    pBt = (p == 0) ? mul2(B, dt2) : fma2(B, dt2, pBt);
                 }
                 if (EXC) {
                     const float2 nv = mul2(NB, r2);                  // -beta r~^2
@@ -156,9 +161,10 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
                 }
             }
             if (COL) {
-                cB = add2(cB, pB);
-                if (!BGT) cBr = add2(cBr, pBr);
-                cBt = add2(cBt, pBt);
+                if (BGT) {
+                    cB = add2(cB, pB);
+                    cBt = add2(cBt, pBt);
+                }
                 const int src = (lane + 1) & 31;
                 cB.x = __shfl_sync(0xffffffffu, cB.x, src);
                 cB.y = __shfl_sync(0xffffffffu, cB.y, src);
@@ -175,7 +181,7 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
             if (!BGT) atomicAdd(colacc + 1 * TC + ch * 32 + lane, cBr.x + cBr.y);
             atomicAdd(colacc + 2 * TC + ch * 32 + lane, cBt.x + cBt.y);
         }
-        fold_rows<RP>(rr, racc);
+        if (BGT) fold_rows<RP>(rr, racc);
     }
 }
 
@@ -188,8 +194,9 @@ struct Geo {
     static constexpr size_t SMEM_TILES = 2 * TC * sizeof(Rec);
     static constexpr size_t SMEM_COLACC = 2 * 3 * TC * sizeof(float);
     static constexpr size_t SMEM_LOHI = 2 * THREADS * R * sizeof(int);
-    static constexpr size_t SMEM_RACC = 3 * RP * THREADS * sizeof(float4);
-    static constexpr size_t SMEM = SMEM_TILES + SMEM_COLACC + SMEM_LOHI + SMEM_RACC;
+    static constexpr size_t SMEM_RACC = 3 * RP * THREADS * sizeof(float4);  // BGT kernels only
+    static constexpr size_t SMEM = SMEM_TILES + SMEM_COLACC + SMEM_LOHI;
+    static constexpr size_t smem(bool bgt) { return SMEM + (bgt ? SMEM_RACC : 0); }
 };
 
 enum { MODE_WIN = 0, MODE_SYM = 1, MODE_BATCH = 2 };
@@ -308,7 +315,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
             rr.yh[p] = f2(-b0.z, -b1.z);
             rr.yl[p] = f2(-c0.x, -c1.x);
             rr.sB[p] = rr.sBr[p] = rr.sBt[p] = rr.sE[p] = rr.sEt[p] = rr.sEq[p] = f2(0.f, 0.f);
-            for (int q = 0; q < 3; ++q) racc[(3 * p + q) * THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (BGT)
+                for (int q = 0; q < 3; ++q) racc[(3 * p + q) * THREADS] = make_float4(0.f, 0.f, 0.f, 0.f);
             mylo[2 * p] = plo[i0];
             mylo[2 * p + 1] = plo[i1];
             myhi[2 * p] = phi[i0];
@@ -404,13 +412,22 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 for (int h = 0; h < 2; ++h) {
                     const int64_t i = r0 + lane + 64 * p + 32 * h;
                     if (i >= n || (!SYM && (i < row_begin || i >= row_end))) continue;
-                    // racc holds (SB, SBr), (SBt, SE), (SEt, SEq) of rows (x, y)
-                    const float4 a = racc[(3 * p + 0) * THREADS];
-                    const float4 b = racc[(3 * p + 1) * THREADS];
-                    const float4 e = racc[(3 * p + 2) * THREADS];
-                    const float vB = h ? a.y : a.x, vBr = h ? a.w : a.z;
-                    const float vBt = h ? b.y : b.x, vE = h ? b.w : b.z;
-                    const float vEt = h ? e.y : e.x, vEq = h ? e.w : e.z;
+                    float vB, vBr, vBt, vE, vEt, vEq;
+                    if (BGT) {  // racc holds (SB, SBr), (SBt, SE), (SEt, SEq) of rows (x, y)
+                        const float4 a = racc[(3 * p + 0) * THREADS];
+                        const float4 b = racc[(3 * p + 1) * THREADS];
+                        const float4 e = racc[(3 * p + 2) * THREADS];
+                        vB = h ? a.y : a.x; vBr = h ? a.w : a.z;
+                        vBt = h ? b.y : b.x; vE = h ? b.w : b.z;
+                        vEt = h ? e.y : e.x; vEq = h ? e.w : e.z;
+                    } else {
+                        vB = h ? rr.sB[p].y : rr.sB[p].x;
+                        vBr = h ? rr.sBr[p].y : rr.sBr[p].x;
+                        vBt = h ? rr.sBt[p].y : rr.sBt[p].x;
+                        vE = h ? rr.sE[p].y : rr.sE[p].x;
+                        vEt = h ? rr.sEt[p].y : rr.sEt[p].x;
+                        vEq = h ? rr.sEq[p].y : rr.sEq[p].x;
+                    }
                     if (vB != 0.f || vBr != 0.f || vBt != 0.f) {
                         atomicAdd(acc + 0 * npad + i, static_cast<double>(vB));
                         atomicAdd(acc + 1 * npad + i, static_cast<double>(vBr) * sr);
@@ -452,7 +469,7 @@ struct Variant {
 
 #define HK_VARIANT(RP, MINB, U, BGT)                                                          \
     {RP, MINB, k_sweep<RP, MINB, U, MODE_WIN, BGT>, k_sweep<RP, MINB, U, MODE_SYM, BGT>,      \
-     k_sweep<RP, MINB, U, MODE_BATCH, BGT>, Geo<RP>::SMEM, Geo<RP>::TR}
+     k_sweep<RP, MINB, U, MODE_BATCH, BGT>, Geo<RP>::smem(BGT), Geo<RP>::TR}
 // (rows-per-lane pairs, resident CTAs per SM, unroll of the 32-step pair loop)
 #define HK_SWEEP_VARIANTS(BGT)                                                               \
     {HK_VARIANT(4, 1, 8, BGT), HK_VARIANT(4, 1, 16, BGT), HK_VARIANT(4, 1, 32, BGT),          \

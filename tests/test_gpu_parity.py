@@ -325,3 +325,16 @@ def test_bg_time_with_underflow_skip(hk):
     ref, rows = oracle_rows(ds, bg_time=True)
     ll, g = hk.loglik_grad(P0, HAWKES_F32 | HAWKES_BG_TIME | HAWKES_SKIP_UNDERFLOW)
     assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, "bg_time + skip")
+
+
+@pytest.mark.parametrize("bg_time", [False, True])
+def test_integer_days_100k_against_fp64_path(hk, bg_time):
+    """N = 100,000 on integer days (runs of equal time gaps, the regime where
+    long FP32 summation chains drift), FP32 path against the FP64 path (which
+    the tests above hold to 1e-10 of the oracle), at the FP32 tolerances."""
+    ds = synth.integer_day_times(synth.grid_dataset(100_000, 300.0, 20, 20, seed=5))
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    fl = HAWKES_BG_TIME if bg_time else 0
+    ref, rows = hk.loglik_rows(P0, HAWKES_F64 | fl)
+    ll, g = hk.loglik_grad(P0, HAWKES_F32 | fl)
+    assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, f"integer days 100k bg_time={bg_time}")
