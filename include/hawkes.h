@@ -58,7 +58,8 @@ enum {
     HAWKES_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
     HAWKES_ERR_OOM = -6,        /* device allocation failed */
     HAWKES_ERR_STATE = -7,      /* call out of order (e.g. no events set) */
-    HAWKES_ERR_TOO_LARGE = -8   /* size above the fixed limit of hawkes_loglik_grad_noalloc */
+    HAWKES_ERR_TOO_LARGE = -8,  /* size above the fixed limit of hawkes_loglik_grad_noalloc */
+    HAWKES_ERR_IO = -9          /* a file could not be written (autotuner cache) */
 };
 
 /* Flags for the log-likelihood calls. */
@@ -222,6 +223,49 @@ int hawkes_tune(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags, in
                 int* chosen, double* ms);
 
 /*
+ * Autotuner cache.  A JSON file maps a configuration key to the tuned
+ * choice, so that a process on a device and problem shape tuned before skips
+ * the search.  The library writes the file as one JSON object with one entry
+ * per line:
+ *   {
+ *   "<key>": {"variant": 0, "chunk": 16, "order": 0, "ms": 365.359, "nvariants": 5},
+ *   ...
+ *   }
+ * The tuners below build the key as
+ *   "<device name>|sm_<major><minor>|single|n<=2^<e>|flags=<flags>"
+ *   "<device name>|sm_<major><minor>|batch|P=<P>|pairs<=2^<e>|flags=<flags>"
+ * where 2^e is the smallest power of two >= n (single problem) or >= the
+ * batch's total number of unordered pairs.  Entries written by a build with a
+ * different number of sweep variants ("nvariants") are ignored, and lines
+ * that do not parse are skipped, so a stale or damaged file only causes cache
+ * misses.  Writes go to "<path>.tmp" and are renamed over the file.
+ *
+ * hawkes_tune_cached: look the context's key up in cache_path; on a hit,
+ * select the cached variant (*from_cache = 1); on a miss, run hawkes_tune
+ * (arguments as there) and store the result (*from_cache = 0).  *chosen
+ * receives the variant.  Returns HAWKES_ERR_IO if the result was chosen but
+ * could not be stored.
+ */
+int hawkes_tune_cached(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags, int reps,
+                       const char* cache_path, int* chosen, int* from_cache);
+
+/*
+ * Host-only access to a cache file (no device is touched).
+ *   hawkes_tune_cache_get: 1 if `key` has a valid entry (outputs, each
+ *     optional, receive it), 0 if the file or the key is missing,
+ *     HAWKES_ERR_ARG for a NULL path or a key containing '"', '\' or a
+ *     control character.
+ *   hawkes_tune_cache_put: insert or replace `key`; HAWKES_ERR_ARG for a bad
+ *     key, a variant outside [0, hawkes_sweep_variants()), a negative chunk
+ *     or order, or a negative or NaN time; HAWKES_ERR_IO if the file cannot
+ *     be written.
+ */
+int hawkes_tune_cache_get(const char* cache_path, const char* key, int* variant, int* chunk,
+                          int* order, double* ms);
+int hawkes_tune_cache_put(const char* cache_path, const char* key, int variant, int chunk,
+                          int order, double ms);
+
+/*
  * Batched evaluation (many problems in one persistent launch).
  *
  * A batch groups P >= 1 contexts on one device, each with its own events
@@ -285,6 +329,16 @@ int hawkes_batch_tune(hawkes_batch* batch, const hawkes_params* d_params, double
 
 /* Select the sweep variant, chunk length and item order directly (drops a captured graph). */
 int hawkes_batch_set_config(hawkes_batch* batch, int variant, int chunk, int order);
+
+/*
+ * As hawkes_batch_tune, through the autotuner cache (see hawkes_tune_cached
+ * for the file and the key).  On a hit the cached configuration is selected
+ * without timing (*from_cache = 1); on a miss the search runs and its result
+ * is stored.  Outputs (optional) as for hawkes_batch_tune, without the time.
+ */
+int hawkes_batch_tune_cached(hawkes_batch* batch, const hawkes_params* d_params, double* d_out,
+                             int reps, const char* cache_path, int* variant, int* chunk,
+                             int* order, int* from_cache);
 
 /*
  * Surrogate network (no counterpart in the paper: the learned part layered on

@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libhawkes.so")
-SOURCES = ["sweep.cu", "sweep_bgt.cu", "api.cu", "kernels.cu", "batch.cu", "mlp.cu", "noalloc.cu"]
+SOURCES = ["sweep.cu", "sweep_bgt.cu", "api.cu", "kernels.cu", "batch.cu", "mlp.cu", "noalloc.cu",
+           "tune_cache.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

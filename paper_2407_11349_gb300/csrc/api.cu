@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -252,6 +253,7 @@ const char* hawkes_strerror(int status) {
         case HAWKES_ERR_OOM: return "device out of memory";
         case HAWKES_ERR_STATE: return "call out of order";
         case HAWKES_ERR_TOO_LARGE: return "size above the fixed scratch limit of the allocation-free entry point";
+        case HAWKES_ERR_IO: return "file could not be written";
         default: return "unknown status";
     }
 }
@@ -564,3 +566,37 @@ int hawkes_profile_read(hawkes_ctx* c, hawkes_profile* out) {
 }
 
 }  // extern "C"
+
+namespace hk {
+int tune_cache_get(const char* path, const char* key, int* variant, int* chunk, int* order,
+                   double* ms);
+int tune_cache_put(const char* path, const char* key, int variant, int chunk, int order, double ms);
+int log2_ceil(double v);
+std::string device_key();
+}  // namespace hk
+
+int hawkes_tune_cached(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int reps,
+                       const char* cache_path, int* chosen, int* from_cache) {
+    using namespace hk;
+    if (!c || !p || reps < 1 || !cache_path) return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    if (!params_ok(p) || (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64))) != 0)
+        return HAWKES_ERR_ARG;
+    DeviceGuard g(c->device);
+    const std::string dk = device_key();
+    if (dk.empty()) return HAWKES_ERR_CUDA;
+    const std::string key = dk + "single|n<=2^" + std::to_string(log2_ceil(static_cast<double>(c->n))) +
+                            "|flags=" + std::to_string(flags);
+    int v = -1;
+    if (tune_cache_get(cache_path, key.c_str(), &v, nullptr, nullptr, nullptr) == 1) {
+        HK_TRY(select_variant(c, v));
+        if (chosen) *chosen = v;
+        if (from_cache) *from_cache = 1;
+        return HAWKES_OK;
+    }
+    std::vector<double> ms(sweep_num_variants());
+    HK_TRY(hawkes_tune(c, p, flags, reps, &v, ms.data()));
+    if (chosen) *chosen = v;
+    if (from_cache) *from_cache = 0;
+    return tune_cache_put(cache_path, key.c_str(), v, CHUNK, 0, ms[v]);
+}

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -32,6 +33,11 @@ cudaError_t launch_sweep_batch(cudaStream_t st, int variant, int grid, const Pro
 __global__ void k_set_u64(uint64_t* dst, uint64_t v) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
 }
+int tune_cache_get(const char* path, const char* key, int* variant, int* chunk, int* order,
+                   double* ms);
+int tune_cache_put(const char* path, const char* key, int variant, int chunk, int order, double ms);
+int log2_ceil(double v);
+std::string device_key();
 }  // namespace hk
 
 using namespace hk;
@@ -345,3 +351,33 @@ int hawkes_batch_set_config(hawkes_batch* b, int variant, int chunk, int order) 
 }
 
 }  // extern "C"
+
+int hawkes_batch_tune_cached(hawkes_batch* b, const hawkes_params* d_params, double* d_out,
+                             int reps, const char* cache_path, int* variant, int* chunk,
+                             int* order, int* from_cache) {
+    if (!b || !d_params || !d_out || reps < 1 || !cache_path) return HAWKES_ERR_ARG;
+    DeviceGuard g(b->device);
+    const std::string dk = device_key();
+    if (dk.empty()) return HAWKES_ERR_CUDA;
+    double pairs = 0.0;
+    for (const hawkes_ctx* c : b->probs) pairs += 0.5 * static_cast<double>(c->n) * (c->n - 1);
+    const std::string key = dk + "batch|P=" + std::to_string(b->probs.size()) + "|pairs<=2^" +
+                            std::to_string(log2_ceil(pairs > 1.0 ? pairs : 1.0)) +
+                            "|flags=" + std::to_string(b->flags);
+    int v = -1, ch = 0, o = 0;
+    if (tune_cache_get(cache_path, key.c_str(), &v, &ch, &o, nullptr) == 1 && ch >= 1 && o <= 1) {
+        HB_TRY(hawkes_batch_set_config(b, v, ch, o));
+        if (variant) *variant = v;
+        if (chunk) *chunk = ch;
+        if (order) *order = o;
+        if (from_cache) *from_cache = 1;
+        return HAWKES_OK;
+    }
+    double ms = 0.0;
+    HB_TRY(hawkes_batch_tune(b, d_params, d_out, reps, &v, &ch, &o, &ms));
+    if (variant) *variant = v;
+    if (chunk) *chunk = ch;
+    if (order) *order = o;
+    if (from_cache) *from_cache = 0;
+    return tune_cache_put(cache_path, key.c_str(), v, ch, o, ms);
+}

@@ -68,6 +68,13 @@ _SIGS = {
     "hawkes_get_sweep_variant": (ctypes.c_int, [_VP]),
     "hawkes_tune": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_params), ctypes.c_uint32, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int), _D]),
+    "hawkes_tune_cached": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_params), ctypes.c_uint32, ctypes.c_int,
+                                          ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "hawkes_tune_cache_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D]),
+    "hawkes_tune_cache_put": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_double]),
     "hawkes_loglik_grad_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, _VP,
                                                   ctypes.c_uint32, _VP, _VP]),
     "hawkes_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int32,
@@ -80,6 +87,9 @@ _SIGS = {
     "hawkes_batch_tune": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D]),
     "hawkes_batch_set_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "hawkes_batch_tune_cached": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_char_p,
+                                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "hawkes_mlp_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_uint64]),
     "hawkes_mlp_destroy": (None, [_VP]),
     "hawkes_mlp_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
@@ -237,6 +247,32 @@ def hawkes_tune(ctx, params, flags=HAWKES_F32, reps=2):
     return ch.value, ms
 
 
+def hawkes_tune_cached(ctx, params, cache_path, flags=HAWKES_F32, reps=2):
+    """Autotune through the JSON cache at ``cache_path`` (see include/hawkes.h).
+    Returns (chosen variant, True if it came from the cache)."""
+    ch, hit = ctypes.c_int(-1), ctypes.c_int(0)
+    p = as_params(params)
+    _check(lib().hawkes_tune_cached(ctx, ctypes.byref(p), int(flags), int(reps), os.fsencode(cache_path),
+                                    ctypes.byref(ch), ctypes.byref(hit)), "hawkes_tune_cached")
+    return ch.value, bool(hit.value)
+
+
+def hawkes_tune_cache_get(cache_path, key):
+    """(variant, chunk, order, ms) stored under ``key``, or None (host only)."""
+    v, c, o, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    rc = lib().hawkes_tune_cache_get(os.fsencode(cache_path), key.encode(), ctypes.byref(v), ctypes.byref(c),
+                                     ctypes.byref(o), ctypes.byref(ms))
+    if rc < 0:
+        _check(rc, "hawkes_tune_cache_get")
+    return (v.value, c.value, o.value, ms.value) if rc == 1 else None
+
+
+def hawkes_tune_cache_put(cache_path, key, variant, chunk, order, ms):
+    """Insert or replace ``key`` in the cache file (host only)."""
+    _check(lib().hawkes_tune_cache_put(os.fsencode(cache_path), key.encode(), int(variant), int(chunk),
+                                       int(order), float(ms)), "hawkes_tune_cache_put")
+
+
 HAWKES_NOALLOC_MAX_N = 65536
 
 
@@ -287,6 +323,16 @@ def hawkes_batch_tune(b, d_params, d_out, reps=1):
     return v.value, c.value, o.value, ms.value
 
 
+def hawkes_batch_tune_cached(b, d_params, d_out, cache_path, reps=1):
+    """Batch autotune through the JSON cache.  Returns (variant, chunk tiles,
+    item order, True if it came from the cache)."""
+    v, c, o, hit = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().hawkes_batch_tune_cached(b, _VP(int(d_params)), _VP(int(d_out)), int(reps),
+                                          os.fsencode(cache_path), ctypes.byref(v), ctypes.byref(c),
+                                          ctypes.byref(o), ctypes.byref(hit)), "hawkes_batch_tune_cached")
+    return v.value, c.value, o.value, bool(hit.value)
+
+
 def hawkes_batch_set_config(b, variant, chunk, order=1):
     _check(lib().hawkes_batch_set_config(b, int(variant), int(chunk), int(order)), "hawkes_batch_set_config")
 
@@ -323,6 +369,9 @@ class Batch:
 
     def set_config(self, variant, chunk, order=1):
         hawkes_batch_set_config(self.b, variant, chunk, order)
+
+    def tune_cached(self, d_params, d_out, cache_path, reps=1):
+        return hawkes_batch_tune_cached(self.b, d_params, d_out, cache_path, reps)
 
 
 HAWKES_MLP_NPARAMS = 69639
@@ -458,6 +507,9 @@ class Hawkes:
 
     def tune(self, params, flags=HAWKES_F32, reps=2):
         return hawkes_tune(self.ctx, params, flags, reps)
+
+    def tune_cached(self, params, cache_path, flags=HAWKES_F32, reps=2):
+        return hawkes_tune_cached(self.ctx, params, cache_path, flags, reps)
 
     def set_variant(self, v):
         hawkes_set_sweep_variant(self.ctx, v)

@@ -134,3 +134,27 @@ def test_batch_time_only_background(problems):
             _close(got[p], *ref[p], f"time-only background problem {p}")
     finally:
         b.close()
+
+
+def test_batch_tune_cached(problems, tmp_path):
+    torch, dss, params, hks, seeds, streams = problems
+    P = len(dss)
+    dp = torch.tensor(params, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+    path = str(tmp_path / "tune.json")
+    b = Batch(hks, seeds, streams, HAWKES_F32)
+    try:
+        first = b.tune_cached(dp.data_ptr(), dout.data_ptr(), path)
+        assert first[3] is False
+        b.set_config(0, 16, 1)
+        second = b.tune_cached(dp.data_ptr(), dout.data_ptr(), path)
+        assert second[3] is True and second[:3] == first[:3]
+        torch.cuda.synchronize()
+        b.run(dp.data_ptr(), 4, dout.data_ptr())
+        b.wait()
+        got = dout.cpu().numpy()
+        ref = _sequential(hks, params, seeds, streams, 4)
+        for p in range(P):
+            _close(got[p], *ref[p], f"cached configuration problem {p}")
+    finally:
+        b.close()

@@ -338,3 +338,24 @@ def test_integer_days_100k_against_fp64_path(hk, bg_time):
     ref, rows = hk.loglik_rows(P0, HAWKES_F64 | fl)
     ll, g = hk.loglik_grad(P0, HAWKES_F32 | fl)
     assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, f"integer days 100k bg_time={bg_time}")
+
+
+def test_tune_cache_on_the_device(hk, tmp_path):
+    """The first cached tune searches and stores, the second reads the file:
+    same variant, selected on the context, under the documented key."""
+    import json
+    from paper_2407_11349_gb300.hawkes import hawkes_get_sweep_variant, hawkes_sweep_variants
+    ds = small_grid(20000, seed=13)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    path = str(tmp_path / "tune.json")
+    v1, hit1 = hk.tune_cached(P0, path, reps=1)
+    assert not hit1 and 0 <= v1 < hawkes_sweep_variants()
+    hk.set_variant((v1 + 1) % hawkes_sweep_variants())
+    v2, hit2 = hk.tune_cached(P0, path, reps=1)
+    assert hit2 and v2 == v1 and hawkes_get_sweep_variant(hk.ctx) == v1
+    doc = json.load(open(path))
+    (key,) = doc
+    assert key.endswith("|single|n<=2^15|flags=0") and "|sm_10" in key
+    v3, hit3 = hk.tune_cached(P0, path, flags=HAWKES_BG_TIME, reps=1)  # another key: a miss
+    assert not hit3 and len(json.load(open(path))) == 2
+    hk.set_variant(0)
