@@ -226,6 +226,19 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
     n0 = tgt.n_exact
     d_su, acc_su, t_su = su.sample(draws, field)
     ev_su = tgt.n_exact - n0
+    # the anchored surrogate: each iteration's field is shifted by the exact
+    # minus the network's gradient at a fixed anchor (the median of the
+    # training points) under that iteration's locations; 3 exact evaluations
+    # per iteration
+    anchor = np.median(X, axis=0)
+    sa = hmc.Sampler(tgt, hmc.Prior(eta0), q_start, n_leapfrog=leapfrog, seed=7, cut=cut)
+    sa.eps, sa.iteration = eps, ex.iteration
+    sa.set_cov(cov)
+    n0 = tgt.n_exact
+    d_sa, acc_sa, t_sa = sa.sample(draws, field, anchor=anchor)
+    ev_sa = tgt.n_exact - n0
+    s_sa = dg.summary(d_sa, hmc.NAMES)
+    ess_sa = min(v["bulk_ess"] for v in s_sa.values())
     # the paper's sampler: univariate Metropolis-Hastings, same target and start
     mh = hmc.MHSampler(tgt, hmc.Prior(eta0), q_start, seed=6, cut=cut)
     mh.iteration = ex.iteration
@@ -241,6 +254,8 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
     ess_su = min(v["bulk_ess"] for v in s_su.values())
     z = {k: abs(s_ex[k]["mean"] - s_su[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_su[k]["mcse"])
          for k in hmc.NAMES}
+    za = {k: abs(s_ex[k]["mean"] - s_sa[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_sa[k]["mcse"])
+          for k in hmc.NAMES}
     net.close()
     tgt.close()
     return {"n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
@@ -250,6 +265,10 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
             "surrogate": {"min_bulk_ess": ess_su, "seconds": t_su, "ess_per_s": ess_su / t_su,
                           "ess_per_s_incl_warmup_and_training": ess_su / (t_su + t_warm + t_train),
                           "accept": float(acc_su.mean()), "exact_evals": ev_su},
+            "surrogate_anchored": {"min_bulk_ess": ess_sa, "seconds": t_sa, "ess_per_s": ess_sa / t_sa,
+                                   "accept": float(acc_sa.mean()), "exact_evals": ev_sa,
+                                   "speedup_ess_per_s": (ess_sa / t_sa) / (ess_ex / t_ex),
+                                   "mean_diff_in_mcse_units": {k: float(v) for k, v in za.items()}},
             "univariate_mh": {"min_bulk_ess": ess_mh, "seconds": t_mh, "ess_per_s": ess_mh / t_mh,
                               "accept": float(acc_mh.mean()), "exact_evals": ev_mh},
             "speedup_ess_per_s": (ess_su / t_su) / (ess_ex / t_ex),

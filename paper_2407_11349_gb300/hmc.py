@@ -15,6 +15,18 @@ and accepts with the EXACT Hamiltonian at both ends under the current X, so
 the chain still targets p(Theta | X, t); a poor surrogate costs acceptance,
 not correctness.
 
+Anchored surrogate (cut posterior).  The network sees only Theta, so it
+predicts the likelihood surface averaged over location draws, while the
+exact surface moves with every draw of X.  With an anchor point a (fixed
+for the whole run, e.g. a warmup estimate of the posterior mean), each
+iteration evaluates the exact gradient at a under the freshly drawn X and
+adds the constant c = grad_exact(a; X) - grad_net(a) to the network's
+field for that iteration's trajectory.  c depends on X and a only, never on
+the chain's state, so the field is still a fixed conservative field during
+the trajectory and the exact accept step keeps p(Theta | X, t) invariant;
+the shift removes the part of the X-dependence that is locally a change of
+slope.  Cost: one more exact evaluation per iteration (3 instead of 2).
+
 Chains advance in lockstep: the exact evaluations of all chains are one
 batched launch (``Batch``), the surrogate's predictions one network call.
 Step size: dual averaging (Hoffman and Gelman 2014); metric: a dense
@@ -213,14 +225,23 @@ class Sampler:
     def _velocity(self, p):
         return np.einsum("cij,cj->ci", self.cov, p)
 
-    def transition(self, field=None):
+    def transition(self, field=None, anchor=None):
         """One cut-posterior iteration: new locations, then one HMC move.
         field(eta) -> (loglik, grad) drives the trajectory (None: exact).
+        anchor (6,) or (C, 6), with a field: shift the field by the exact
+        minus the field's gradient at the anchor under this iteration's
+        locations (see the module notes).
         A trajectory that leaves |eta| <= ETA_MAX or turns non-finite is
         divergent: it is rejected (its exact evaluations use the current
         state instead).  Returns the acceptance probability of each chain."""
         self.iteration += 1
         lp0, g0 = self._exact(self.q, resample=self.cut)
+        shift = 0.0
+        if field is not None and anchor is not None:
+            a_pt = np.array(np.broadcast_to(anchor, self.q.shape), dtype=np.float64)
+            _, g_a = self.target.eval(a_pt)  # exact, under the locations just drawn
+            shift = g_a - field(a_pt)[1]
+            shift = np.where(np.isfinite(shift), shift, 0.0)
         p0 = self._momentum()
         # a random step size per iteration (independent of the state) avoids
         # trajectories that return to their start on near-Gaussian targets
@@ -236,7 +257,7 @@ class Sampler:
             if field is None:
                 lp, g = self._exact(safe(q))
             else:
-                lp, g = None, field(safe(q))[1] + self.prior(safe(q))[1]
+                lp, g = None, field(safe(q))[1] + shift + self.prior(safe(q))[1]
             bad[:] |= ~np.all(np.isfinite(g), axis=1)
             return lp, np.where(bad[:, None], 0.0, g)
 
@@ -260,7 +281,7 @@ class Sampler:
         self.divergent = int(bad.sum())
         return a
 
-    def warmup(self, n, field=None):
+    def warmup(self, n, field=None, anchor=None):
         """Adapt the step size (dual averaging, every iteration) and the dense
         metric: a fast window (first 15%), slow windows of doubling length
         whose draws give a covariance estimate (shrunk towards its diagonal),
@@ -276,7 +297,7 @@ class Sampler:
             b, w = e, 2 * w
         draws, last_start = [], start
         for k in range(n):
-            a = self.transition(field)
+            a = self.transition(field, anchor)
             self.eps = da.update(a)
             for (w0, w1) in bounds:
                 if w0 <= k < w1:
@@ -295,12 +316,12 @@ class Sampler:
         self.eps = da.final()
         return last_start
 
-    def sample(self, n, field=None):
+    def sample(self, n, field=None, anchor=None):
         out = np.zeros((self.C, n, 6))
         acc = np.zeros(n)
         t0 = time.perf_counter()
         for k in range(n):
-            acc[k] = self.transition(field).mean()
+            acc[k] = self.transition(field, anchor).mean()
             out[:, k] = self.q
         return out, acc, time.perf_counter() - t0
 

@@ -58,6 +58,21 @@ def test_surrogate_hmc_matches_exact_and_saves_exact_evaluations():
         ess_su = min(s_su[nm]["bulk_ess"] for nm in hmc.NAMES)
         # exact-kernel evaluations per effective sample: the network's gain
         assert exact_evals_su / ess_su < 0.5 * exact_evals_ex / ess_ex
+
+        # the anchored field (shifted by the exact minus the network's gradient
+        # at a fixed point) targets the same posterior
+        sa = hmc.Sampler(tgt, hmc.Prior(eta0), ex.q.copy(), n_leapfrog=L, seed=6, cut=False)
+        sa.eps = ex.eps.copy()
+        sa.set_cov(ex.cov)
+        n0 = tgt.n_exact
+        d_sa, acc_sa, _ = sa.sample(600, field, anchor=np.median(X, axis=0))
+        assert tgt.n_exact - n0 == 600 * 3 * C
+        s_sa = dg.summary(d_sa, hmc.NAMES)
+        for nm in hmc.NAMES:
+            diff = abs(s_ex[nm]["mean"] - s_sa[nm]["mean"])
+            se = np.hypot(s_ex[nm]["mcse"], s_sa[nm]["mcse"])
+            assert diff < 4.5 * se, (nm, s_ex[nm], s_sa[nm])
+        assert acc_sa.mean() > 0.6
         net.close()
     finally:
         tgt.close()

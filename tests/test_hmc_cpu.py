@@ -138,3 +138,59 @@ def test_univariate_mh_recovers_gaussian_posterior():
         x = draws[:, :, k]
         assert abs(x.mean() - mean[k]) < 4.5 * summ[nm]["mcse"], (nm, x.mean(), mean[k])
         assert abs(x.var() / var[k] - 1) < 0.3
+
+
+def test_anchored_surrogate_removes_a_slope_error_and_stays_exact():
+    """A surrogate whose gradient is off by a constant (what a change of the
+    locations does to the slope) is made exact by the anchor shift:
+    acceptance returns to the exact-HMC level and the posterior is right."""
+    bias = 3.0 / S
+
+    def field(eta):
+        return None, -(eta - M) / S ** 2 + bias
+
+    draws0, acc0, _ = _run(field, seed=4, n=1500)
+    C = 4
+    tgt = GaussTarget(M, S, C)
+    smp = hmc.Sampler(tgt, hmc.Prior(ETA0), np.tile(M, (C, 1)) + 0.01, n_leapfrog=8, seed=4)
+    smp.warmup(300)
+    n0 = tgt.n_exact
+    draws, acc, _ = smp.sample(1500, field, anchor=M + 0.5 * S)
+    assert tgt.n_exact - n0 == 1500 * 3 * C  # start, anchor, end
+    ex, acc_ex, _ = _run(None, seed=4, n=300)
+    assert acc.mean() > acc0.mean() + 0.1
+    assert abs(acc.mean() - acc_ex.mean()) < 0.05
+    _check_posterior(draws)
+
+
+class CutGaussTarget(GaussTarget):
+    """Each location draw adds a random slope x . eta / s to the
+    log-likelihood (x ~ N(0, 0.5^2) per chain and iteration)."""
+
+    def __init__(self, m, s, C, seed=0):
+        super().__init__(m, s, C)
+        self.rng = np.random.default_rng(seed)
+        self.x = np.zeros((C, 6))
+
+    def eval(self, eta):
+        ll, g = super().eval(eta)
+        return ll + np.sum(self.x * eta / self.s, axis=1), g + self.x / self.s
+
+    def resample_eval(self, iteration, eta):
+        self.x = 0.5 * self.rng.standard_normal((self.C, 6))
+        return self.eval(eta)
+
+
+def test_anchored_surrogate_raises_acceptance_under_the_cut_scheme():
+    def field(eta):  # the draw-averaged surface
+        return None, -(eta - M) / S ** 2
+
+    acc = {}
+    for anchored in (False, True):
+        C = 4
+        tgt = CutGaussTarget(M, S, C, seed=5)
+        smp = hmc.Sampler(tgt, hmc.Prior(ETA0), np.tile(M, (C, 1)) + 0.01, n_leapfrog=8, seed=5)
+        smp.warmup(300)
+        _, a, _ = smp.sample(600, field, anchor=M if anchored else None)
+        acc[anchored] = a.mean()
+    assert acc[True] > acc[False] + 0.1, acc
