@@ -21,7 +21,11 @@
  *    no C++ exception crosses this interface.
  *  - The caller owns every pointer it passes.  Host arrays are copied before
  *    the call returns.  Device pointers (the *_async calls) must stay valid
- *    until the work queued on the context's stream has finished.
+ *    until the work queued on the context's stream has finished, and must be
+ *    8-byte aligned (they point at doubles); a misaligned one is rejected
+ *    with HAWKES_ERR_ARG before any work is queued.
+ *  - Each call that does work opens an NVTX range named after the call, so
+ *    Nsight timelines show the library's calls (no cost without a tool).
  *  - Units are the caller's (the test workloads use km and days); times must
  *    be > 0 and non-decreasing, every value finite.
  *  - A device-side failure (a bounded wait that gave up, a non-finite result)
@@ -122,7 +126,9 @@ int hawkes_set_events(hawkes_ctx* ctx, int64_t n, const double* t, const double*
  * convex polygon or any other partition).
  *   tri_county[n_tri]  county of each triangle, non-decreasing; every county
  *                      of hawkes_set_events needs triangles of positive total area
- *   tri_xy[6 n_tri]    vertices ax, ay, bx, by, cx, cy of each triangle
+ *   tri_xy[6 n_tri]    vertices ax, ay, bx, by, cx, cy of each triangle (finite)
+ * A county id out of range or out of order, a non-finite vertex, or a county
+ * without positive area returns HAWKES_ERR_ARG and leaves no counties set.
  */
 int hawkes_set_counties(hawkes_ctx* ctx, int32_t n_tri, const int32_t* tri_county,
                         const double* tri_xy);

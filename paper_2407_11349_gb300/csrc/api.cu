@@ -21,7 +21,7 @@ __global__ void k_rows64(const double*, const double*, const double*, const doub
                          const int32_t*, const int32_t*, const double*, int, int64_t, int64_t,
                          int64_t, int64_t, int, const int*, int*, double*, double*, double*);
 __global__ void k_reduce(const double*, int, const double*, const double*, double*, int*);
-__global__ void k_tri_area(const double*, int32_t, double*);
+__global__ void k_tri_area(const double*, int32_t, double*, int*);
 __global__ void k_tri_county(const int32_t*, int32_t, int32_t, double*, int32_t*, int32_t*, int*);
 __global__ void k_tri_check(const int32_t*, int32_t, int32_t, int*);
 __global__ void k_resample(const int32_t*, int64_t, const double*, const double*, const int32_t*,
@@ -259,6 +259,7 @@ const char* hawkes_strerror(int status) {
 }
 
 int hawkes_create(hawkes_ctx** out, int device, void* cuda_stream) {
+    HK_NVTX("hawkes_create");
     if (!out) return HAWKES_ERR_ARG;
     *out = nullptr;
     int ndev = 0;
@@ -320,6 +321,7 @@ int hawkes_create(hawkes_ctx** out, int device, void* cuda_stream) {
 }
 
 void hawkes_destroy(hawkes_ctx* c) {
+    HK_NVTX("hawkes_destroy");
     if (!c) return;
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
@@ -339,6 +341,7 @@ int64_t hawkes_num_events(const hawkes_ctx* c) { return c ? c->n : 0; }
 
 int hawkes_set_events(hawkes_ctx* c, int64_t n, const double* t, const double* x, const double* y,
                       const int32_t* county, int32_t n_counties, const double* county_scale) {
+    HK_NVTX("hawkes_set_events");
     if (!c || n < 1 || !t || !county || n_counties < 1 || !county_scale) return HAWKES_ERR_ARG;
     if ((x == nullptr) != (y == nullptr)) return HAWKES_ERR_ARG;
     if (n > (int64_t(1) << 31) - 2 * NPAD_MULT) return HAWKES_ERR_ARG;  // 32-bit event indices
@@ -393,6 +396,7 @@ int hawkes_set_events(hawkes_ctx* c, int64_t n, const double* t, const double* x
 
 int hawkes_set_counties(hawkes_ctx* c, int32_t n_tri, const int32_t* tri_county,
                         const double* tri_xy) {
+    HK_NVTX("hawkes_set_counties");
     if (!c || n_tri < 1 || !tri_county || !tri_xy) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
@@ -420,7 +424,7 @@ int hawkes_set_counties(hawkes_ctx* c, int32_t n_tri, const int32_t* tri_county,
     if (rc == HAWKES_OK) rc = take_device_error(c);
     if (rc == HAWKES_OK)
         rc = timed(c, HAWKES_K_OTHER, [&] {
-            k_tri_area<<<grid_for(c, n_tri), 256, 0, st>>>(c->tri_xy, n_tri, c->tri_cum);
+            k_tri_area<<<grid_for(c, n_tri), 256, 0, st>>>(c->tri_xy, n_tri, c->tri_cum, c->ctr);
         });
     if (rc == HAWKES_OK)
         rc = timed(c, HAWKES_K_OTHER, [&] {
@@ -437,6 +441,7 @@ int hawkes_set_counties(hawkes_ctx* c, int32_t n_tri, const int32_t* tri_county,
 }
 
 int hawkes_resample_locations(hawkes_ctx* c, uint64_t seed, uint64_t stream, uint64_t iteration) {
+    HK_NVTX("hawkes_resample_locations");
     if (!c) return HAWKES_ERR_ARG;
     if (c->n == 0 || !c->counties_ok) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
@@ -448,6 +453,7 @@ int hawkes_resample_locations(hawkes_ctx* c, uint64_t seed, uint64_t stream, uin
 }
 
 int hawkes_get_locations(hawkes_ctx* c, double* x, double* y) {
+    HK_NVTX("hawkes_get_locations");
     if (!c || !x || !y) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
@@ -459,6 +465,7 @@ int hawkes_get_locations(hawkes_ctx* c, double* x, double* y) {
 
 int hawkes_loglik_grad(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int64_t row_begin,
                        int64_t row_end, double* loglik, double* grad) {
+    HK_NVTX("hawkes_loglik_grad");
     if (!c || !p || !loglik || !grad) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
     if (row_begin < 0 || row_end > c->n || row_begin >= row_end) return HAWKES_ERR_ARG;
@@ -472,7 +479,8 @@ int hawkes_loglik_grad(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, in
 
 int hawkes_loglik_grad_async(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
                              double* d_out) {
-    if (!c || !d_params || !d_out) return HAWKES_ERR_ARG;
+    HK_NVTX("hawkes_loglik_grad_async");
+    if (!c || !d_params || !d_out || !aligned8(d_params) || !aligned8(d_out)) return HAWKES_ERR_ARG;
     if ((flags & ~kFlagsAll) != 0) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
@@ -481,6 +489,7 @@ int hawkes_loglik_grad_async(hawkes_ctx* c, const hawkes_params* d_params, uint3
 
 int hawkes_loglik_rows(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, double* out7,
                        double* rows) {
+    HK_NVTX("hawkes_loglik_rows");
     if (!c || !p || !out7 || !rows) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
     DeviceGuard g(c->device);
@@ -488,6 +497,7 @@ int hawkes_loglik_rows(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, do
 }
 
 int hawkes_check_bounded_wait(hawkes_ctx* c, double* seconds) {
+    HK_NVTX("hawkes_check_bounded_wait");
     if (!c) return HAWKES_ERR_ARG;
     DeviceGuard g(c->device);
     HK_CUDA(cudaStreamSynchronize(c->stream));
@@ -508,6 +518,7 @@ int hawkes_check_bounded_wait(hawkes_ctx* c, double* seconds) {
 int hawkes_sweep_variants(void) { return sweep_num_variants(); }
 
 int hawkes_set_sweep_variant(hawkes_ctx* c, int variant) {
+    HK_NVTX("hawkes_set_sweep_variant");
     if (!c) return HAWKES_ERR_ARG;
     DeviceGuard g(c->device);
     HK_CUDA(cudaStreamSynchronize(c->stream));
@@ -518,6 +529,7 @@ int hawkes_get_sweep_variant(const hawkes_ctx* c) { return c ? c->variant : HAWK
 
 int hawkes_tune(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int reps, int* chosen,
                 double* ms) {
+    HK_NVTX("hawkes_tune");
     if (!c || !p || reps < 1) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
     if (!params_ok(p) || (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64))) != 0)
@@ -549,6 +561,7 @@ int hawkes_tune(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int reps,
 }
 
 int hawkes_profile_enable(hawkes_ctx* c, int on) {
+    HK_NVTX("hawkes_profile_enable");
     if (!c) return HAWKES_ERR_ARG;
     DeviceGuard g(c->device);
     HK_CUDA(cudaStreamSynchronize(c->stream));
@@ -558,6 +571,7 @@ int hawkes_profile_enable(hawkes_ctx* c, int on) {
 }
 
 int hawkes_profile_read(hawkes_ctx* c, hawkes_profile* out) {
+    HK_NVTX("hawkes_profile_read");
     if (!c || !out) return HAWKES_ERR_ARG;
     DeviceGuard g(c->device);
     HK_CUDA(cudaStreamSynchronize(c->stream));
@@ -577,6 +591,7 @@ std::string device_key();
 
 int hawkes_tune_cached(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int reps,
                        const char* cache_path, int* chosen, int* from_cache) {
+    HK_NVTX("hawkes_tune_cached");
     using namespace hk;
     if (!c || !p || reps < 1 || !cache_path) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;

@@ -183,6 +183,7 @@ extern "C" {
 int hawkes_batch_create(hawkes_batch** out, hawkes_ctx* const* problems, int32_t n_problems,
                         const uint64_t* seeds, const uint64_t* streams, uint32_t flags,
                         void* cuda_stream) {
+    HK_NVTX("hawkes_batch_create");
     if (!out) return HAWKES_ERR_ARG;
     *out = nullptr;
     if (!problems || n_problems < 1 ||
@@ -244,6 +245,7 @@ int hawkes_batch_create(hawkes_batch** out, hawkes_ctx* const* problems, int32_t
 }
 
 void hawkes_batch_destroy(hawkes_batch* b) {
+    HK_NVTX("hawkes_batch_destroy");
     if (!b) return;
     DeviceGuard g(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
@@ -261,7 +263,8 @@ void hawkes_batch_destroy(hawkes_batch* b) {
 
 int hawkes_batch_run(hawkes_batch* b, const hawkes_params* d_params, uint64_t iteration,
                      double* d_out) {
-    if (!b || !d_params || !d_out) return HAWKES_ERR_ARG;
+    HK_NVTX("hawkes_batch_run");
+    if (!b || !d_params || !d_out || !aligned8(d_params) || !aligned8(d_out)) return HAWKES_ERR_ARG;
     DeviceGuard g(b->device);
     k_set_u64<<<1, 32, 0, b->stream>>>(b->d_iter, iteration);
     HB_CUDA(cudaGetLastError());
@@ -271,7 +274,8 @@ int hawkes_batch_run(hawkes_batch* b, const hawkes_params* d_params, uint64_t it
 }
 
 int hawkes_batch_capture(hawkes_batch* b, const hawkes_params* d_params, double* d_out) {
-    if (!b || !d_params || !d_out) return HAWKES_ERR_ARG;
+    HK_NVTX("hawkes_batch_capture");
+    if (!b || !d_params || !d_out || !aligned8(d_params) || !aligned8(d_out)) return HAWKES_ERR_ARG;
     DeviceGuard g(b->device);
     HB_CUDA(cudaStreamSynchronize(b->stream));
     drop_graph(b);
@@ -296,6 +300,7 @@ int hawkes_batch_capture(hawkes_batch* b, const hawkes_params* d_params, double*
 }
 
 int hawkes_batch_wait(hawkes_batch* b) {
+    HK_NVTX("hawkes_batch_wait");
     if (!b) return HAWKES_ERR_ARG;
     DeviceGuard g(b->device);
     HB_CUDA(cudaStreamSynchronize(b->stream));
@@ -304,7 +309,9 @@ int hawkes_batch_wait(hawkes_batch* b) {
 
 int hawkes_batch_tune(hawkes_batch* b, const hawkes_params* d_params, double* d_out, int reps,
                       int* variant, int* chunk, int* order, double* best_ms) {
-    if (!b || !d_params || !d_out || reps < 1) return HAWKES_ERR_ARG;
+    HK_NVTX("hawkes_batch_tune");
+    if (!b || !d_params || !d_out || !aligned8(d_params) || !aligned8(d_out) || reps < 1)
+        return HAWKES_ERR_ARG;
     DeviceGuard g(b->device);
     static const int kChunks[] = {16, 32, 64};
     int bv = -1, bc = 0, bo = 0;
@@ -342,6 +349,7 @@ int hawkes_batch_tune(hawkes_batch* b, const hawkes_params* d_params, double* d_
 }
 
 int hawkes_batch_set_config(hawkes_batch* b, int variant, int chunk, int order) {
+    HK_NVTX("hawkes_batch_set_config");
     if (!b || variant < 0 || variant >= sweep_num_variants() || chunk < 1 || order < 0 ||
         order > 1)
         return HAWKES_ERR_ARG;
@@ -355,7 +363,10 @@ int hawkes_batch_set_config(hawkes_batch* b, int variant, int chunk, int order) 
 int hawkes_batch_tune_cached(hawkes_batch* b, const hawkes_params* d_params, double* d_out,
                              int reps, const char* cache_path, int* variant, int* chunk,
                              int* order, int* from_cache) {
-    if (!b || !d_params || !d_out || reps < 1 || !cache_path) return HAWKES_ERR_ARG;
+    HK_NVTX("hawkes_batch_tune_cached");
+    if (!b || !d_params || !d_out || !aligned8(d_params) || !aligned8(d_out) || reps < 1 ||
+        !cache_path)
+        return HAWKES_ERR_ARG;
     DeviceGuard g(b->device);
     const std::string dk = device_key();
     if (dk.empty()) return HAWKES_ERR_CUDA;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "hawkes.h"
@@ -19,6 +20,19 @@ namespace hk {
 //   relative to the first event of their block of TB = TC events.  Event
 //   arrays are padded to a multiple of NPAD_MULT (the largest row tile).
 // ---------------------------------------------------------------------------
+// NVTX range around one C-ABI call (visible in Nsight timelines; a no-op
+// when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define HK_NVTX(name) ::hk::NvtxRange hk_nvtx_range_(name)
+
+// Device pointers handed to the library point at doubles: 8-byte alignment.
+inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
 // Every flag bit the log-likelihood calls accept.
 constexpr uint32_t kFlagsAll = HAWKES_F64 | HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW | HAWKES_BG_TIME;
 

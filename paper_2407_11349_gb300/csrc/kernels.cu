@@ -346,9 +346,11 @@ __global__ void k_reduce(const double* __restrict__ partials, int nparts,
 // Location resample (cut posterior, Sec. 2.2).
 // ---------------------------------------------------------------------------
 // Triangle areas, evaluated exactly as documented (no fused multiply-add).
-__global__ void k_tri_area(const double* __restrict__ xy, int32_t n_tri, double* area) {
+__global__ void k_tri_area(const double* __restrict__ xy, int32_t n_tri, double* area, int* ctr) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_tri; k += gridDim.x * blockDim.x) {
         const double* v = xy + 6 * (int64_t)k;
+        for (int q = 0; q < 6; ++q)
+            if (!isfinite(v[q])) set_error(ctr, HAWKES_ERR_ARG);
         const double cr = __dsub_rn(__dmul_rn(__dsub_rn(v[2], v[0]), __dsub_rn(v[5], v[1])),
                                     __dmul_rn(__dsub_rn(v[4], v[0]), __dsub_rn(v[3], v[1])));
         area[k] = __dmul_rn(0.5, fabs(cr));

@@ -441,6 +441,7 @@ int forward_backward(hawkes_mlp* m, int B, bool train) {
 extern "C" {
 
 int hawkes_mlp_create(hawkes_mlp** out, int device, void* cuda_stream, uint64_t seed) {
+    HK_NVTX("hawkes_mlp_create");
     if (!out) return HAWKES_ERR_ARG;
     *out = nullptr;
     int ndev = 0;
@@ -488,6 +489,7 @@ int hawkes_mlp_create(hawkes_mlp** out, int device, void* cuda_stream, uint64_t 
 }
 
 void hawkes_mlp_destroy(hawkes_mlp* m) {
+    HK_NVTX("hawkes_mlp_destroy");
     if (!m) return;
     DeviceGuard g(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
@@ -504,6 +506,7 @@ void hawkes_mlp_destroy(hawkes_mlp* m) {
 }
 
 int hawkes_mlp_get_params(hawkes_mlp* m, float* params) {
+    HK_NVTX("hawkes_mlp_get_params");
     if (!m || !params) return HAWKES_ERR_ARG;
     DeviceGuard g(m->device);
     HM_CUDA(cudaMemcpyAsync(params, m->P, NPARAMS * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
@@ -511,6 +514,7 @@ int hawkes_mlp_get_params(hawkes_mlp* m, float* params) {
 }
 
 int hawkes_mlp_set_params(hawkes_mlp* m, const float* params) {
+    HK_NVTX("hawkes_mlp_set_params");
     if (!m || !params) return HAWKES_ERR_ARG;
     DeviceGuard g(m->device);
     HM_CUDA(cudaMemcpyAsync(m->P, params, NPARAMS * sizeof(float), cudaMemcpyHostToDevice, m->stream));
@@ -522,6 +526,7 @@ int hawkes_mlp_set_params(hawkes_mlp* m, const float* params) {
 }
 
 int hawkes_mlp_set_data(hawkes_mlp* m, int64_t n, const double* X, const double* Y) {
+    HK_NVTX("hawkes_mlp_set_data");
     if (!m || n < 2 || !X || !Y) return HAWKES_ERR_ARG;
     DeviceGuard g(m->device);
     HM_CUDA(cudaStreamSynchronize(m->stream));
@@ -553,6 +558,7 @@ int hawkes_mlp_set_data(hawkes_mlp* m, int64_t n, const double* X, const double*
 
 int hawkes_mlp_train(hawkes_mlp* m, int64_t steps, int batch, double lr, uint64_t seed,
                      double* last_loss) {
+    HK_NVTX("hawkes_mlp_train");
     if (!m || steps < 0 || batch < 64 || batch > BMAX || batch % 64 != 0 || !(lr > 0)) return HAWKES_ERR_ARG;
     if (!m->have_stats || !m->Xs) return HAWKES_ERR_STATE;
     DeviceGuard g(m->device);
@@ -575,6 +581,7 @@ int hawkes_mlp_train(hawkes_mlp* m, int64_t steps, int batch, double lr, uint64_
 
 int hawkes_mlp_loss_grad(hawkes_mlp* m, int batch, const float* Xs, const float* Ts, double* loss,
                          float* grad, float* Y) {
+    HK_NVTX("hawkes_mlp_loss_grad");
     if (!m || batch < 64 || batch > BMAX || batch % 64 != 0 || !Xs || !Ts) return HAWKES_ERR_ARG;
     DeviceGuard g(m->device);
     cudaStream_t st = m->stream;
@@ -591,7 +598,10 @@ int hawkes_mlp_loss_grad(hawkes_mlp* m, int batch, const float* Xs, const float*
 }
 
 int hawkes_mlp_predict(hawkes_mlp* m, int64_t count, const double* d_logp, double* d_out) {
-    if (!m || count < 1 || count > BMAX || !d_logp || !d_out) return HAWKES_ERR_ARG;
+    HK_NVTX("hawkes_mlp_predict");
+    if (!m || count < 1 || count > BMAX || !d_logp || !d_out || !hk::aligned8(d_logp) ||
+        !hk::aligned8(d_out))
+        return HAWKES_ERR_ARG;
     if (!m->have_stats) return HAWKES_ERR_STATE;
     DeviceGuard g(m->device);
     const int B = static_cast<int>((count + 63) / 64 * 64);
@@ -603,6 +613,7 @@ int hawkes_mlp_predict(hawkes_mlp* m, int64_t count, const double* d_logp, doubl
 }
 
 int hawkes_mlp_stats(hawkes_mlp* m, double* stats26) {
+    HK_NVTX("hawkes_mlp_stats");
     if (!m || !stats26) return HAWKES_ERR_ARG;
     if (!m->have_stats) return HAWKES_ERR_STATE;
     DeviceGuard g(m->device);
@@ -611,6 +622,7 @@ int hawkes_mlp_stats(hawkes_mlp* m, double* stats26) {
 }
 
 int hawkes_mlp_wait(hawkes_mlp* m) {
+    HK_NVTX("hawkes_mlp_wait");
     if (!m) return HAWKES_ERR_ARG;
     DeviceGuard g(m->device);
     return st_of(cudaStreamSynchronize(m->stream));

@@ -186,6 +186,10 @@ extern "C" int hawkes_loglik_grad_noalloc(const double* d_t, const double* d_x, 
                                           const hawkes_params* d_params, uint32_t flags,
                                           double* d_out, void* cuda_stream) {
     if (!d_t || !d_x || !d_y || !d_params || !d_out) return HAWKES_ERR_ARG;
+    for (const void* p : {static_cast<const void*>(d_t), static_cast<const void*>(d_x),
+                          static_cast<const void*>(d_y), static_cast<const void*>(d_s),
+                          static_cast<const void*>(d_params), static_cast<const void*>(d_out)})
+        if (!aligned8(p)) return HAWKES_ERR_ARG;  // NULL d_s is aligned
     if ((flags & ~static_cast<uint32_t>(HAWKES_MODEL1 | HAWKES_BG_TIME)) != 0)
         return HAWKES_ERR_ARG;  // FP32 only
     if (n < 1) return HAWKES_ERR_ARG;
