@@ -63,7 +63,8 @@ enum {
     HAWKES_ERR_OOM = -6,        /* device allocation failed */
     HAWKES_ERR_STATE = -7,      /* call out of order (e.g. no events set) */
     HAWKES_ERR_TOO_LARGE = -8,  /* size above the fixed limit of hawkes_loglik_grad_noalloc */
-    HAWKES_ERR_IO = -9          /* a file could not be written (autotuner cache) */
+    HAWKES_ERR_IO = -9,         /* a file could not be written (autotuner cache) */
+    HAWKES_ERR_BOUNDS = -10     /* HAWKES_DEBUG build: a device-side index check failed */
 };
 
 /* Flags for the log-likelihood calls. */
@@ -419,6 +420,26 @@ int64_t hawkes_num_events(const hawkes_ctx* ctx);
  * designed (*seconds, optional: how long it took), an error otherwise.
  */
 int hawkes_check_bounded_wait(hawkes_ctx* ctx, double* seconds);
+
+/*
+ * Debug build.  Compiled with -DHAWKES_DEBUG (lib/libhawkes_debug.so), the
+ * kernels check every index they derive from a work list or a fix-up list
+ * before using it: a work item must lie inside its problem's causal
+ * triangle and padded arrays, a batch item's problem index must exist, and
+ * a fix-up row must be an event.  A failed check skips the access and
+ * latches HAWKES_ERR_BOUNDS, returned by the next synchronous call.  This is
+ * the library's own stand-in for a memory checker; release builds compile
+ * the checks out.
+ *
+ * hawkes_debug_build: 1 in the debug build, 0 otherwise.
+ * hawkes_debug_set_item: debug build only (else HAWKES_ERR_STATE): overwrite
+ *   work item k of the context's symmetric work list with (row tile,
+ *   first column tile, end column tile), to exercise the checks.  A test
+ *   hook; evaluations use the altered list until the next
+ *   hawkes_set_events or hawkes_set_sweep_variant rebuilds it.
+ */
+int hawkes_debug_build(void);
+int hawkes_debug_set_item(hawkes_ctx* ctx, int k, int row_tile, int col_begin, int col_end);
 
 /*
  * Allocation-free log-likelihood and gradient (no counterpart in the paper;

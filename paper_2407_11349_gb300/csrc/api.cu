@@ -254,6 +254,7 @@ const char* hawkes_strerror(int status) {
         case HAWKES_ERR_STATE: return "call out of order";
         case HAWKES_ERR_TOO_LARGE: return "size above the fixed scratch limit of the allocation-free entry point";
         case HAWKES_ERR_IO: return "file could not be written";
+        case HAWKES_ERR_BOUNDS: return "a device-side index check of the debug build failed";
         default: return "unknown status";
     }
 }
@@ -614,4 +615,18 @@ int hawkes_tune_cached(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, in
     if (chosen) *chosen = v;
     if (from_cache) *from_cache = 0;
     return tune_cache_put(cache_path, key.c_str(), v, CHUNK, 0, ms[v]);
+}
+
+int hawkes_debug_build(void) { return kDebug ? 1 : 0; }
+
+int hawkes_debug_set_item(hawkes_ctx* c, int k, int row_tile, int col_begin, int col_end) {
+    HK_NVTX("hawkes_debug_set_item");
+    if (!kDebug) return HAWKES_ERR_STATE;
+    if (!c || k < 0 || k >= c->nitems || !c->items) return HAWKES_ERR_ARG;
+    DeviceGuard g(c->device);
+    HK_CUDA(cudaStreamSynchronize(c->stream));
+    const int4 it = make_int4(row_tile, col_begin, col_end, 0);
+    HK_CUDA(cudaMemcpy(c->items + k, &it, sizeof(int4), cudaMemcpyHostToDevice));
+    c->items_variant = -1;  // rebuilt by the next variant selection or event set
+    return HAWKES_OK;
 }

@@ -28,7 +28,7 @@ int sweep_num_variants();
 int sweep_blocks_per_sm(int v);
 std::vector<int4> sweep_items_batch(const std::vector<int64_t>& ns, int v, int chunk, int order);
 cudaError_t launch_sweep_batch(cudaStream_t st, int variant, int grid, const ProbDesc* probs,
-                               const int4* items, int nitems, int* ctr, bool bgt);
+                               int nprobs, const int4* items, int nitems, int* ctr, bool bgt);
 
 __global__ void k_set_u64(uint64_t* dst, uint64_t v) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
@@ -142,7 +142,8 @@ int enqueue(hawkes_batch* b, const hawkes_params* d_params, double* d_out, bool 
     }
     HB_CUDA(cudaMemsetAsync(b->d_ctr + CT_WORK, 0, sizeof(int), st));
     if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[0], st));
-    HB_CUDA(launch_sweep_batch(st, b->variant, b->grid, b->d_probs, b->d_items, b->nitems, b->d_ctr,
+    HB_CUDA(launch_sweep_batch(st, b->variant, b->grid, b->d_probs, static_cast<int>(P), b->d_items,
+                               b->nitems, b->d_ctr,
                                bgt));
     if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[1], st));
     for (int p = 0; p < P; ++p) {

@@ -30,6 +30,16 @@ struct NvtxRange {
 };
 #define HK_NVTX(name) ::hk::NvtxRange hk_nvtx_range_(name)
 
+// HAWKES_DEBUG build: kernels check the indices they derive from work lists
+// and fix-up lists before using them; a failed check latches
+// HAWKES_ERR_BOUNDS and skips the access.  Release builds compile the checks
+// out.
+#ifdef HAWKES_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
+
 // Device pointers handed to the library point at doubles: 8-byte alignment.
 inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 

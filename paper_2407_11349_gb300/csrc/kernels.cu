@@ -246,6 +246,10 @@ __global__ void k_finalize(const double* __restrict__ acc, const double* __restr
             const double lam = mu * cB * sums[0] + th * cE * sums[3];
             if (lam < thr) {
                 const int k = atomicAdd(ctr + CT_FIX, 1);
+                if (kDebug && !(k >= 0 && k < npad)) {
+                    set_error(ctr, HAWKES_ERR_BOUNDS);
+                    continue;
+                }
                 fixlist[k] = static_cast<int>(i);
                 continue;
             }
@@ -280,6 +284,10 @@ __global__ void k_rows64(const double* __restrict__ t, const double* __restrict_
     const int64_t total = mode ? static_cast<int64_t>(ctr[CT_FIX]) : count;
     for (int64_t k = blockIdx.x; k < total; k += gridDim.x) {
         const int64_t i = mode ? fixlist[k] : row_begin + k;
+        if (kDebug && !(i >= 0 && i < n && (mode || k < npad))) {
+            if (threadIdx.x == 0) set_error(ctr, HAWKES_ERR_BOUNDS);
+            continue;  // uniform over the block: i depends on k only
+        }
         const double ti = t[i], xi = x[i], yi = y[i];
         const int64_t li = lo[i], hj = hi[i];
         double v[6] = {0, 0, 0, 0, 0, 0};

@@ -103,12 +103,12 @@ cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row
 // One persistent launch over the items of many problems; ctr[CT_WORK] must be
 // zero when it starts.
 cudaError_t launch_sweep_batch(cudaStream_t st, int variant, int grid, const ProbDesc* probs,
-                               const int4* items, int nitems, int* ctr, bool bgt) {
+                               int nprobs, const int4* items, int nitems, int* ctr, bool bgt) {
     const Variant& v = variant_of(variant, bgt);
     if (grid > nitems) grid = nitems;
     if (grid <= 0) return cudaSuccess;
     ProbDesc none{};
-    v.batch<<<grid, THREADS, v.smem, st>>>(none, probs, items, nitems, ctr, 0, 0, 0, 0);
+    v.batch<<<grid, THREADS, v.smem, st>>>(none, probs, items, nitems, ctr, 0, 0, 0, nprobs);
     return cudaGetLastError();
 }
 

@@ -208,6 +208,7 @@ enum { MODE_WIN = 0, MODE_SYM = 1, MODE_BATCH = 2 };
 //               launch, one queue)
 //   MODE_WIN:   item k -> row tile item0 + k / nch, column chunk k % nch of
 //               problem `one`, rows [row_begin, row_end) only
+// In MODE_BATCH, nch is the number of problems (checked in debug builds).
 template <int RP, int MINB, int UNROLL, int MODE, bool BGT>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_sweep(ProbDesc one, const ProbDesc* __restrict__ probs, const int4* __restrict__ items,
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(THREADS, MINB)
     float4* racc = reinterpret_cast<float4*>(smem + G::SMEM_TILES + G::SMEM_COLACC + G::SMEM_LOHI) +
                    threadIdx.x;
     __shared__ __align__(8) uint64_t bars[2];
-    __shared__ int s_item, s_abort;
+    __shared__ int s_item, s_abort, s_bad;
     // The current item's problem.  In batch mode it is re-read from shared
     // memory (volatile: not kept in registers) wherever it is needed outside
     // the pair loop, so the pair loop is compiled as in the one-problem modes.
@@ -251,7 +252,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
         if (tid == 0) {
             const int k = atomicAdd(ctr + CT_WORK, 1);
             s_item = k;
-            if (MODE == MODE_BATCH && k < nitems) {
+            if (kDebug) s_bad = 0;
+            if (kDebug && MODE == MODE_BATCH && k < nitems && !(items[k].w >= 0 && items[k].w < nch)) {
+                s_bad = 1;  // problem index out of range: do not read its descriptor
+            } else if (MODE == MODE_BATCH && k < nitems) {
                 const ProbDesc d = probs[items[k].w];
                 vpd->rec = d.rec; vpd->lo = d.lo; vpd->hi = d.hi; vpd->tb = d.tb;
                 vpd->cc = d.cc; vpd->acc = d.acc; vpd->n = d.n; vpd->npad = d.npad;
@@ -273,6 +277,20 @@ __global__ void __launch_bounds__(THREADS, MINB)
             I = item0 + item / nch;
             jb = (item % nch) * CHUNK;
             je = min(jb + CHUNK, ncol_tiles);
+        }
+        if (kDebug) {  // the item must lie inside its problem's causal triangle
+            bool ok = !s_bad;
+            const int64_t nn = ok ? HK_PD(n) : 0, np = ok ? HK_PD(npad) : 0;
+            const int64_t nI = (nn + G::TR - 1) / G::TR;
+            const int64_t rows_end = SYM ? min((I + 1) * G::TR, nn) : nn;
+            const int64_t jmax = (rows_end + TC - 1) / TC;
+            ok = ok && I >= 0 && I < nI && (I + 1) * G::TR <= np && jb >= 0 && jb < je &&
+                 je <= jmax && static_cast<int64_t>(je) * TC <= np;
+            if (!ok) {
+                if (tid == 0) set_error(ctr, HAWKES_ERR_BOUNDS);
+                __syncthreads();
+                continue;
+            }
         }
         const double* cc = HK_PD(cc);
         if (MODE == MODE_BATCH && cc[CC_VALID] == 0.0) {  // problem with invalid parameters

@@ -15,7 +15,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "lib", "libhawkes.so")
+# HAWKES_DEBUG=1 in the environment selects the debug build (device index
+# checks; built by build.build(debug=True)).
+LIB_PATH = os.path.join(_HERE, "lib", "libhawkes_debug.so" if os.environ.get("HAWKES_DEBUG") == "1"
+                        else "libhawkes.so")
 
 HAWKES_OK = 0
 HAWKES_F32 = 0
@@ -64,6 +67,8 @@ _SIGS = {
     "hawkes_num_events": (ctypes.c_int64, [_VP]),
     "hawkes_sweep_variants": (ctypes.c_int, []),
     "hawkes_check_bounded_wait": (ctypes.c_int, [_VP, _D]),
+    "hawkes_debug_build": (ctypes.c_int, []),
+    "hawkes_debug_set_item": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "hawkes_set_sweep_variant": (ctypes.c_int, [_VP, ctypes.c_int]),
     "hawkes_get_sweep_variant": (ctypes.c_int, [_VP]),
     "hawkes_tune": (ctypes.c_int, [_VP, ctypes.POINTER(hawkes_params), ctypes.c_uint32, ctypes.c_int,
@@ -110,7 +115,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"libhawkes.so not built ({LIB_PATH}); run the package build first")
+            raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run the package build first")
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
             f = getattr(L, name)
@@ -271,6 +276,17 @@ def hawkes_tune_cache_put(cache_path, key, variant, chunk, order, ms):
     """Insert or replace ``key`` in the cache file (host only)."""
     _check(lib().hawkes_tune_cache_put(os.fsencode(cache_path), key.encode(), int(variant), int(chunk),
                                        int(order), float(ms)), "hawkes_tune_cache_put")
+
+
+def hawkes_debug_build():
+    """1 if the loaded library is the HAWKES_DEBUG build."""
+    return int(lib().hawkes_debug_build())
+
+
+def hawkes_debug_set_item(ctx, k, row_tile, col_begin, col_end):
+    """Debug build only: overwrite work item k (a test hook for the checks)."""
+    _check(lib().hawkes_debug_set_item(ctx, int(k), int(row_tile), int(col_begin), int(col_end)),
+           "hawkes_debug_set_item")
 
 
 HAWKES_NOALLOC_MAX_N = 65536
