@@ -239,6 +239,16 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
     ev_sa = tgt.n_exact - n0
     s_sa = dg.summary(d_sa, hmc.NAMES)
     ess_sa = min(v["bulk_ess"] for v in s_sa.values())
+    # three surrogate moves per location draw (1 + 3 exact evaluations per
+    # iteration): each draw's p(Theta | X, t) is mixed further before the next
+    sm = hmc.Sampler(tgt, hmc.Prior(eta0), q_start, n_leapfrog=leapfrog, seed=8, cut=cut)
+    sm.eps, sm.iteration = eps, ex.iteration
+    sm.set_cov(cov)
+    n0 = tgt.n_exact
+    d_sm, acc_sm, t_sm = sm.sample(draws, field, moves=3)
+    ev_sm = tgt.n_exact - n0
+    s_sm = dg.summary(d_sm, hmc.NAMES)
+    ess_sm = min(v["bulk_ess"] for v in s_sm.values())
     # the paper's sampler: univariate Metropolis-Hastings, same target and start
     mh = hmc.MHSampler(tgt, hmc.Prior(eta0), q_start, seed=6, cut=cut)
     mh.iteration = ex.iteration
@@ -256,6 +266,8 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
          for k in hmc.NAMES}
     za = {k: abs(s_ex[k]["mean"] - s_sa[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_sa[k]["mcse"])
           for k in hmc.NAMES}
+    zm = {k: abs(s_ex[k]["mean"] - s_sm[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_sm[k]["mcse"])
+          for k in hmc.NAMES}
     net.close()
     tgt.close()
     return {"n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
@@ -269,6 +281,10 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
                                    "accept": float(acc_sa.mean()), "exact_evals": ev_sa,
                                    "speedup_ess_per_s": (ess_sa / t_sa) / (ess_ex / t_ex),
                                    "mean_diff_in_mcse_units": {k: float(v) for k, v in za.items()}},
+            "surrogate_3_moves": {"min_bulk_ess": ess_sm, "seconds": t_sm, "ess_per_s": ess_sm / t_sm,
+                                  "accept": float(acc_sm.mean()), "exact_evals": ev_sm,
+                                  "speedup_ess_per_s": (ess_sm / t_sm) / (ess_ex / t_ex),
+                                  "mean_diff_in_mcse_units": {k: float(v) for k, v in zm.items()}},
             "univariate_mh": {"min_bulk_ess": ess_mh, "seconds": t_mh, "ess_per_s": ess_mh / t_mh,
                               "accept": float(acc_mh.mean()), "exact_evals": ev_mh},
             "speedup_ess_per_s": (ess_su / t_su) / (ess_ex / t_ex),

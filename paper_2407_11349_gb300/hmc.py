@@ -225,15 +225,18 @@ class Sampler:
     def _velocity(self, p):
         return np.einsum("cij,cj->ci", self.cov, p)
 
-    def transition(self, field=None, anchor=None):
-        """One cut-posterior iteration: new locations, then one HMC move.
-        field(eta) -> (loglik, grad) drives the trajectory (None: exact).
-        anchor (6,) or (C, 6), with a field: shift the field by the exact
-        minus the field's gradient at the anchor under this iteration's
-        locations (see the module notes).
-        A trajectory that leaves |eta| <= ETA_MAX or turns non-finite is
-        divergent: it is rejected (its exact evaluations use the current
-        state instead).  Returns the acceptance probability of each chain."""
+    def transition(self, field=None, anchor=None, moves=1):
+        """One cut-posterior iteration: new locations, then `moves` HMC moves
+        under them (the paper's scheme has one).  field(eta) -> (loglik, grad)
+        drives the trajectories (None: exact).  anchor (6,) or (C, 6), with a
+        field: shift the field by the exact minus the field's gradient at the
+        anchor under this iteration's locations (see the module notes).
+        Every move under the same locations starts from the exact value of
+        the state the previous move left, so a further surrogate move costs
+        one exact evaluation.  A trajectory that leaves |eta| <= ETA_MAX or
+        turns non-finite is divergent: it is rejected (its exact evaluations
+        use the current state instead).  Returns the acceptance probability
+        of each chain, averaged over the moves."""
         self.iteration += 1
         lp0, g0 = self._exact(self.q, resample=self.cut)
         shift = 0.0
@@ -242,8 +245,21 @@ class Sampler:
             _, g_a = self.target.eval(a_pt)  # exact, under the locations just drawn
             shift = g_a - field(a_pt)[1]
             shift = np.where(np.isfinite(shift), shift, 0.0)
+        acc = np.zeros(self.C)
+        self.divergent = 0
+        for _ in range(int(moves)):
+            a, lp0, g0 = self._move(lp0, g0, field, shift)
+            acc += a
+        return acc / int(moves)
+
+    def _move(self, lp0, g0, field, shift):
+        """One HMC move from self.q, whose exact log-posterior and gradient
+        are (lp0, g0) under the current locations.  Returns the acceptance
+        probability and the exact (log-posterior, gradient) of the new state
+        (the gradient is None where a surrogate move was accepted; it is only
+        needed to start exact trajectories)."""
         p0 = self._momentum()
-        # a random step size per iteration (independent of the state) avoids
+        # a random step size per move (independent of the state) avoids
         # trajectories that return to their start on near-Gaussian targets
         eps = (self.eps * (1.0 + self.jitter * (2.0 * self.rng.random(self.C) - 1.0)))[:, None]
         bad = np.zeros(self.C, dtype=bool)
@@ -263,14 +279,14 @@ class Sampler:
 
         q = self.q.copy()
         p = p0 + 0.5 * eps * (g0 if field is None else grad(q)[1])
-        lp1 = None
+        lp1, g1 = None, None
         for step in range(self.L):
             q = q + eps * self._velocity(p)
             lpq, gq = grad(q)
             p = p + (eps if step < self.L - 1 else 0.5 * eps) * gq
-            lp1 = lpq
+            lp1, g1 = lpq, gq
         if field is not None:
-            lp1, _ = self._exact(safe(q))
+            lp1, g1 = self._exact(safe(q))
         H0 = -lp0 + self._kinetic(p0)
         H1 = -lp1 + self._kinetic(p)
         log_a = np.where(np.isfinite(H1) & ~bad, H0 - H1, -np.inf)
@@ -278,10 +294,12 @@ class Sampler:
         u = self.rng.random(self.C)
         take = (u < a) & ~bad
         self.q[take] = q[take]
-        self.divergent = int(bad.sum())
-        return a
+        self.divergent += int(bad.sum())
+        lp_new = np.where(take, lp1, lp0)
+        g_new = np.where(take[:, None], g1, g0) if (g1 is not None and g0 is not None) else None
+        return a, lp_new, g_new
 
-    def warmup(self, n, field=None, anchor=None):
+    def warmup(self, n, field=None, anchor=None, moves=1):
         """Adapt the step size (dual averaging, every iteration) and the dense
         metric: a fast window (first 15%), slow windows of doubling length
         whose draws give a covariance estimate (shrunk towards its diagonal),
@@ -297,7 +315,7 @@ class Sampler:
             b, w = e, 2 * w
         draws, last_start = [], start
         for k in range(n):
-            a = self.transition(field, anchor)
+            a = self.transition(field, anchor, moves)
             self.eps = da.update(a)
             for (w0, w1) in bounds:
                 if w0 <= k < w1:
@@ -316,12 +334,12 @@ class Sampler:
         self.eps = da.final()
         return last_start
 
-    def sample(self, n, field=None, anchor=None):
+    def sample(self, n, field=None, anchor=None, moves=1):
         out = np.zeros((self.C, n, 6))
         acc = np.zeros(n)
         t0 = time.perf_counter()
         for k in range(n):
-            acc[k] = self.transition(field, anchor).mean()
+            acc[k] = self.transition(field, anchor, moves).mean()
             out[:, k] = self.q
         return out, acc, time.perf_counter() - t0
 

@@ -194,3 +194,23 @@ def test_anchored_surrogate_raises_acceptance_under_the_cut_scheme():
         _, a, _ = smp.sample(600, field, anchor=M if anchored else None)
         acc[anchored] = a.mean()
     assert acc[True] > acc[False] + 0.1, acc
+
+
+def test_several_moves_per_location_draw_stay_exact_and_cost_one_evaluation_each():
+    """moves=3: three surrogate HMC moves under each location draw; each
+    further move starts from the exact value of the state the last one left,
+    so an iteration costs 1 + 3 exact evaluations, and the posterior is
+    unchanged."""
+    def field(eta):  # biased surrogate, as above
+        d = (eta - (M + 0.3 * S)) / (1.3 * S)
+        return None, -d / (1.3 * S)
+
+    C = 4
+    tgt = GaussTarget(M, S, C)
+    smp = hmc.Sampler(tgt, hmc.Prior(ETA0), np.tile(M, (C, 1)) + 0.01, n_leapfrog=8, seed=8)
+    smp.warmup(300)
+    n0 = tgt.n_exact
+    draws, acc, _ = smp.sample(1500, field, moves=3)
+    assert tgt.n_exact - n0 == 1500 * (1 + 3) * C
+    assert 0.05 < acc.mean() < 0.99
+    _check_posterior(draws, rhat_max=1.1)
