@@ -185,7 +185,7 @@ def bench_batch(ds_c3, steps, warmup):
                       "N=5,000..200,000 (sum 899,416); one persistent launch in a CUDA graph"}
 
 
-def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
+def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, ref_rounds=0):
     """Min bulk ESS per second of exact HMC vs surrogate HMC, same data, same
     adapted step size and metric.  cut=True: locations resampled every
     iteration (the cut-posterior scheme); cut=False: locations held fixed,
@@ -268,9 +268,28 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300):
           for k in hmc.NAMES}
     zm = {k: abs(s_ex[k]["mean"] - s_sm[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_sm[k]["mcse"])
           for k in hmc.NAMES}
+    ref = None
+    if cut and ref_rounds > 0:
+        # the cut posterior itself: exact HMC with each location draw held
+        # fixed, pooled over ref_rounds x chains draws of X
+        t0 = time.perf_counter()
+        d_ref = hmc.cut_posterior_reference(tgt, hmc.Prior(eta0), q_start, cov, eps, ref_rounds,
+                                            burn=30, draws=100, n_leapfrog=leapfrog, seed=11)
+        m_cr = d_ref.mean(axis=1)  # one mean per (chain, round)
+        ref_mean = m_cr.mean(axis=0)
+        ref_se = m_cr.std(axis=0, ddof=1) / np.sqrt(m_cr.shape[0])
+        summ = {"exact": s_ex, "surrogate": s_su, "surrogate_anchored": s_sa, "surrogate_3_moves": s_sm}
+        ref = {"location_draws": int(m_cr.shape[0]), "draws_per_location": int(d_ref.shape[1]),
+               "seconds": time.perf_counter() - t0,
+               "mean": {k: float(ref_mean[i]) for i, k in enumerate(hmc.NAMES)},
+               "se": {k: float(ref_se[i]) for i, k in enumerate(hmc.NAMES)},
+               "diff_in_se_units": {nm: {k: float(abs(sm[k]["mean"] - ref_mean[i]) /
+                                                  np.hypot(sm[k]["mcse"], ref_se[i]))
+                                         for i, k in enumerate(hmc.NAMES)}
+                                    for nm, sm in summ.items()}}
     net.close()
     tgt.close()
-    return {"n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
+    return {"cut_posterior_reference": ref, "n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
             "draws_per_chain": draws, "training_pairs": int(X.shape[0]), "train_loss": loss,
             "exact": {"min_bulk_ess": ess_ex, "seconds": t_ex, "ess_per_s": ess_ex / t_ex,
                       "accept": float(acc_ex.mean()), "exact_evals": ev_ex},
@@ -378,6 +397,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 30-chain batch measurement")
+    ap.add_argument("--hmc-cut-reference", type=int, default=6,
+                    help="location draws per chain for the independent cut-posterior reference (0: off)")
     ap.add_argument("--hmc-n", type=int, default=50_000,
                     help="events for the HMC ESS/s comparison (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=4)
@@ -552,7 +573,7 @@ def main():
         if world == 1 and not args.no_batch and args.workload == "c3":
             out["batch30"] = bench_batch(ds, steps=3, warmup=1)
         if world == 1 and args.hmc_n > 0 and args.workload == "c3":
-            out["hmc"] = {"cut_posterior": bench_hmc(args.hmc_n, cut=True),
+            out["hmc"] = {"cut_posterior": bench_hmc(args.hmc_n, cut=True, ref_rounds=args.hmc_cut_reference),
                           "fixed_locations": bench_hmc(args.hmc_n, cut=False)}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ds)

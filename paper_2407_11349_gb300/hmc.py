@@ -419,6 +419,29 @@ class MHSampler:
         return out, acc, time.perf_counter() - t0
 
 
+def cut_posterior_reference(target, prior, q_start, cov, eps, rounds, burn, draws, n_leapfrog=10,
+                            seed=0, first_iteration=10_000):
+    """Draws from the cut posterior itself, the mixture over location draws X
+    of p(Theta | X, t) (Sec. 2.2), independent of how well one MCMC move
+    mixes under one X: for each of `rounds` rounds, draw new locations for
+    every chain (resample counter first_iteration + round), then run exact HMC
+    with those locations held fixed (`burn` moves, then `draws` kept), which
+    samples p(Theta | X, t) exactly.  Returns (C * rounds, draws, 6): one
+    chain per (chain, round), each with its own X."""
+    C = q_start.shape[0]
+    out = []
+    for r in range(rounds):
+        target.resample_eval(first_iteration + r, q_start)  # new X for every chain
+        smp = Sampler(target, prior, q_start, n_leapfrog=n_leapfrog, seed=seed + r, cut=False)
+        smp.eps = np.array(eps, dtype=np.float64, copy=True)
+        smp.set_cov(cov)
+        for _ in range(burn):
+            smp.transition()
+        d, _, _ = smp.sample(draws)
+        out.append(d)
+    return np.concatenate(out, axis=0)
+
+
 def save(path, sampler, mlp=None, train_X=None, train_Y=None):
     """Checkpoint the sampler (and the surrogate: weights + its training set,
     from which its standardisation is recomputed) to an .npz file."""

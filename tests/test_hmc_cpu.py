@@ -214,3 +214,25 @@ def test_several_moves_per_location_draw_stay_exact_and_cost_one_evaluation_each
     assert tgt.n_exact - n0 == 1500 * (1 + 3) * C
     assert 0.05 < acc.mean() < 0.99
     _check_posterior(draws, rhat_max=1.1)
+
+
+def test_cut_posterior_reference_matches_the_mixture_in_closed_form():
+    """Exact HMC under each of many location draws, pooled, is the cut
+    posterior: for the random-slope toy, a Gaussian mixture whose mean is the
+    fixed-X posterior mean and whose variance adds Var(x / s) / P^2."""
+    C = 4
+    tgt = CutGaussTarget(M, S, C, seed=9)
+    prior = hmc.Prior(ETA0)
+    smp = hmc.Sampler(tgt, prior, np.tile(M, (C, 1)) + 0.01, n_leapfrog=8, seed=9, cut=False)
+    smp.warmup(200)
+    d = hmc.cut_posterior_reference(tgt, prior, smp.q.copy(), smp.cov, smp.eps, rounds=40, burn=20,
+                                    draws=60, n_leapfrog=8, seed=3)
+    assert d.shape == (C * 40, 60, 6)
+    P = 1 / S ** 2 + 1 / hmc.PRIOR_SD ** 2
+    mean = (M / S ** 2 + ETA0 / hmc.PRIOR_SD ** 2 + 1.0) / P
+    var = 1 / P + 0.25 / (S ** 2 * P ** 2)
+    m_cr = d.mean(axis=1)
+    se = m_cr.std(axis=0, ddof=1) / np.sqrt(m_cr.shape[0])
+    assert np.all(np.abs(m_cr.mean(axis=0) - mean) < 4.5 * se), (m_cr.mean(axis=0), mean, se)
+    pooled = d.reshape(-1, 6).var(axis=0)
+    assert np.all(np.abs(pooled / var - 1) < 0.25), (pooled, var)
