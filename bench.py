@@ -32,7 +32,10 @@ METRIC = "loglik+grad pairs/s at N=1M (1 and 30-chain batch); HMC ESS/s surrogat
 UNIT = "pairs/s"
 WORKLOAD = "c3: N=1,000,000 events, 1,200 d, 3,143 Voronoi counties (4,500x2,800 km), resample + FP32 loglik + 6-dim grad per step"
 # Algorithmic FP32 pipe operations per unordered pair (one lane op each:
-# FADD, FMUL or FFMA), excluding the two-word coordinate split; see the design doc.
+# FADD, FMUL or FFMA): time difference 1, dx and dy 2, r^2 2, dt^2 1,
+# background exponent 1, row and column background moments 3 + 3, beta r^2 1,
+# excitation exponent 2, excitation moments 3.  The two-word coordinate split
+# (4 more) is overhead, not counted.
 ALG_FP32_OPS_PER_PAIR = 19
 FP32_LANES_PER_SM = 128
 
@@ -185,25 +188,33 @@ def bench_batch(ds_c3, steps, warmup):
                       "N=5,000..200,000 (sum 899,416); one persistent launch in a CUDA graph"}
 
 
-def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, ref_rounds=0):
+def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, ref_rounds=0,
+              lite=False, flags=0):
     """Min bulk ESS per second of exact HMC vs surrogate HMC, same data, same
     adapted step size and metric.  cut=True: locations resampled every
     iteration (the cut-posterior scheme); cut=False: locations held fixed,
     so both samplers target p(Theta | X, t) exactly and their posterior
     means must agree within Monte Carlo error.  The surrogate is trained on
     the exact evaluations of the exact-HMC warmup from its last slow
-    adaptation window on."""
+    adaptation window on.  Unless lite, three more samplers run from the
+    same start: the anchored surrogate, three surrogate moves per location
+    draw, and the paper's univariate Metropolis-Hastings.  ref_rounds > 0
+    (cut only): every sampler is also compared with an independent sample
+    of the cut posterior.  flags: extra likelihood flags (e.g. the exact
+    underflow skip, which changes no result)."""
     from paper_2407_11349_gb300 import diagnostics as dg
     from paper_2407_11349_gb300 import hmc, synth
     from paper_2407_11349_gb300.hawkes import MLP
 
     # events with the model's space-time structure on a 40 x 40 grid of 50 km
-    # counties over 1,200 days (the posterior is then identified; see DESIGN.md)
+    # counties over 1,200 days (drawn from the model itself, so the posterior
+    # is concentrated near the generating parameters)
     ds = synth.clustered_dataset(n_events, T=1200.0, nx=40, ny=40, seed=4)
     eta0 = np.log(synth.DEFAULT_PARAMS)
-    tgt = hmc.HawkesTarget(ds, chains, seed=4)
+    prior = hmc.Prior(eta0)
+    tgt = hmc.HawkesTarget(ds, chains, seed=4, flags=flags)
     init = np.tile(eta0, (chains, 1)) + np.random.default_rng(4).normal(0, 0.01, (chains, 6))
-    ex = hmc.Sampler(tgt, hmc.Prior(eta0), init, n_leapfrog=leapfrog, seed=1, cut=cut)
+    ex = hmc.Sampler(tgt, prior, init, n_leapfrog=leapfrog, seed=1, cut=cut)
     ex.record = []
     t0 = time.perf_counter()
     last = ex.warmup(warmup)
@@ -216,103 +227,83 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     loss = net.train(4000, batch=512, lr=1e-3, seed=3)
     t_train = time.perf_counter() - t0
     q_start, eps, cov = ex.q.copy(), ex.eps.copy(), ex.cov.copy()
-    n0 = tgt.n_exact
-    d_ex, acc_ex, t_ex = ex.sample(draws)
-    ev_ex = tgt.n_exact - n0
-    su = hmc.Sampler(tgt, hmc.Prior(eta0), q_start, n_leapfrog=leapfrog, seed=5, cut=cut)
-    su.eps, su.iteration = eps, ex.iteration
-    su.set_cov(cov)
     field = hmc.SurrogateField(net, chains)
-    n0 = tgt.n_exact
-    d_su, acc_su, t_su = su.sample(draws, field)
-    ev_su = tgt.n_exact - n0
-    # the anchored surrogate: each iteration's field is shifted by the exact
-    # minus the network's gradient at a fixed anchor (the median of the
-    # training points) under that iteration's locations; 3 exact evaluations
-    # per iteration
-    anchor = np.median(X, axis=0)
-    sa = hmc.Sampler(tgt, hmc.Prior(eta0), q_start, n_leapfrog=leapfrog, seed=7, cut=cut)
-    sa.eps, sa.iteration = eps, ex.iteration
-    sa.set_cov(cov)
-    n0 = tgt.n_exact
-    d_sa, acc_sa, t_sa = sa.sample(draws, field, anchor=anchor)
-    ev_sa = tgt.n_exact - n0
-    s_sa = dg.summary(d_sa, hmc.NAMES)
-    ess_sa = min(v["bulk_ess"] for v in s_sa.values())
-    # three surrogate moves per location draw (1 + 3 exact evaluations per
-    # iteration): each draw's p(Theta | X, t) is mixed further before the next
-    sm = hmc.Sampler(tgt, hmc.Prior(eta0), q_start, n_leapfrog=leapfrog, seed=8, cut=cut)
-    sm.eps, sm.iteration = eps, ex.iteration
-    sm.set_cov(cov)
-    n0 = tgt.n_exact
-    d_sm, acc_sm, t_sm = sm.sample(draws, field, moves=3)
-    ev_sm = tgt.n_exact - n0
-    s_sm = dg.summary(d_sm, hmc.NAMES)
-    ess_sm = min(v["bulk_ess"] for v in s_sm.values())
-    # the paper's sampler: univariate Metropolis-Hastings, same target and start
-    mh = hmc.MHSampler(tgt, hmc.Prior(eta0), q_start, seed=6, cut=cut)
-    mh.iteration = ex.iteration
-    mh.log_scale = np.log(np.sqrt(np.stack([np.diag(c) for c in cov]))) + np.log(2.38 / np.sqrt(6.0))
-    mh.warmup(50)
-    n0 = tgt.n_exact
-    d_mh, acc_mh, t_mh = mh.sample(draws)
-    ev_mh = tgt.n_exact - n0
-    s_mh = dg.summary(d_mh, hmc.NAMES)
-    ess_mh = min(v["bulk_ess"] for v in s_mh.values())
-    s_ex, s_su = dg.summary(d_ex, hmc.NAMES), dg.summary(d_su, hmc.NAMES)
-    ess_ex = min(v["bulk_ess"] for v in s_ex.values())
-    ess_su = min(v["bulk_ess"] for v in s_su.values())
-    z = {k: abs(s_ex[k]["mean"] - s_su[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_su[k]["mcse"])
-         for k in hmc.NAMES}
-    za = {k: abs(s_ex[k]["mean"] - s_sa[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_sa[k]["mcse"])
-          for k in hmc.NAMES}
-    zm = {k: abs(s_ex[k]["mean"] - s_sm[k]["mean"]) / np.hypot(s_ex[k]["mcse"], s_sm[k]["mcse"])
-          for k in hmc.NAMES}
+
+    def run(sampler, **kw):
+        n0 = tgt.n_exact
+        d, acc, sec = sampler.sample(draws, **kw)
+        summ = dg.summary(d, hmc.NAMES)
+        ess = min(v["bulk_ess"] for v in summ.values())
+        return summ, {"min_bulk_ess": ess, "seconds": sec, "ess_per_s": ess / sec,
+                      "accept": float(acc.mean()), "exact_evals": tgt.n_exact - n0,
+                      "exact_evals_per_ess": (tgt.n_exact - n0) / max(ess, 1e-9)}
+
+    def hmc_sampler(seed):
+        smp = hmc.Sampler(tgt, prior, q_start, n_leapfrog=leapfrog, seed=seed, cut=cut)
+        smp.eps, smp.iteration = eps, ex.iteration
+        smp.set_cov(cov)
+        return smp
+
+    summaries, res = {}, {}
+    summaries["exact"], res["exact"] = run(ex)
+    summaries["surrogate"], res["surrogate"] = run(hmc_sampler(5), field=field)
+    if not lite:
+        # the anchored surrogate: each iteration's field is shifted by the
+        # exact minus the network's gradient at a fixed anchor (the median of
+        # the training points) under that iteration's locations
+        summaries["surrogate_anchored"], res["surrogate_anchored"] = run(
+            hmc_sampler(7), field=field, anchor=np.median(X, axis=0))
+        # three surrogate moves per location draw (1 + 3 exact evaluations)
+        summaries["surrogate_3_moves"], res["surrogate_3_moves"] = run(hmc_sampler(8), field=field,
+                                                                       moves=3)
+        # the paper's sampler: univariate Metropolis-Hastings, same target and start
+        mh = hmc.MHSampler(tgt, prior, q_start, seed=6, cut=cut)
+        mh.iteration = ex.iteration
+        mh.log_scale = np.log(np.sqrt(np.stack([np.diag(c) for c in cov]))) + np.log(2.38 / np.sqrt(6.0))
+        mh.warmup(50)
+        summaries["univariate_mh"], res["univariate_mh"] = run(mh)
+    s_ex = summaries["exact"]
+    for k, summ in summaries.items():
+        res[k]["ess_per_s_vs_exact"] = res[k]["ess_per_s"] / res["exact"]["ess_per_s"]
+        if k != "exact":
+            res[k]["mean_diff_vs_exact_in_mcse_units"] = {
+                nm: float(abs(s_ex[nm]["mean"] - summ[nm]["mean"]) / np.hypot(s_ex[nm]["mcse"], summ[nm]["mcse"]))
+                for nm in hmc.NAMES}
     ref = None
     if cut and ref_rounds > 0:
         # the cut posterior itself: exact HMC with each location draw held
         # fixed, pooled over ref_rounds x chains draws of X
         t0 = time.perf_counter()
-        d_ref = hmc.cut_posterior_reference(tgt, hmc.Prior(eta0), q_start, cov, eps, ref_rounds,
-                                            burn=30, draws=100, n_leapfrog=leapfrog, seed=11)
+        d_ref = hmc.cut_posterior_reference(tgt, prior, q_start, cov, eps, ref_rounds, burn=30, draws=100,
+                                            n_leapfrog=leapfrog, seed=11)
         m_cr = d_ref.mean(axis=1)  # one mean per (chain, round)
         ref_mean = m_cr.mean(axis=0)
         ref_se = m_cr.std(axis=0, ddof=1) / np.sqrt(m_cr.shape[0])
-        summ = {"exact": s_ex, "surrogate": s_su, "surrogate_anchored": s_sa, "surrogate_3_moves": s_sm}
         ref = {"location_draws": int(m_cr.shape[0]), "draws_per_location": int(d_ref.shape[1]),
                "seconds": time.perf_counter() - t0,
                "mean": {k: float(ref_mean[i]) for i, k in enumerate(hmc.NAMES)},
                "se": {k: float(ref_se[i]) for i, k in enumerate(hmc.NAMES)},
-               "diff_in_se_units": {nm: {k: float(abs(sm[k]["mean"] - ref_mean[i]) /
-                                                  np.hypot(sm[k]["mcse"], ref_se[i]))
+               "diff_in_se_units": {nm: {k: float(abs(sm[k]["mean"] - ref_mean[i]) / np.hypot(sm[k]["mcse"],
+                                                                                             ref_se[i]))
                                          for i, k in enumerate(hmc.NAMES)}
-                                    for nm, sm in summ.items()}}
+                                    for nm, sm in summaries.items() if nm != "univariate_mh"}}
     net.close()
     tgt.close()
-    return {"cut_posterior_reference": ref, "n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
-            "draws_per_chain": draws, "training_pairs": int(X.shape[0]), "train_loss": loss,
-            "exact": {"min_bulk_ess": ess_ex, "seconds": t_ex, "ess_per_s": ess_ex / t_ex,
-                      "accept": float(acc_ex.mean()), "exact_evals": ev_ex},
-            "surrogate": {"min_bulk_ess": ess_su, "seconds": t_su, "ess_per_s": ess_su / t_su,
-                          "ess_per_s_incl_warmup_and_training": ess_su / (t_su + t_warm + t_train),
-                          "accept": float(acc_su.mean()), "exact_evals": ev_su},
-            "surrogate_anchored": {"min_bulk_ess": ess_sa, "seconds": t_sa, "ess_per_s": ess_sa / t_sa,
-                                   "accept": float(acc_sa.mean()), "exact_evals": ev_sa,
-                                   "speedup_ess_per_s": (ess_sa / t_sa) / (ess_ex / t_ex),
-                                   "mean_diff_in_mcse_units": {k: float(v) for k, v in za.items()}},
-            "surrogate_3_moves": {"min_bulk_ess": ess_sm, "seconds": t_sm, "ess_per_s": ess_sm / t_sm,
-                                  "accept": float(acc_sm.mean()), "exact_evals": ev_sm,
-                                  "speedup_ess_per_s": (ess_sm / t_sm) / (ess_ex / t_ex),
-                                  "mean_diff_in_mcse_units": {k: float(v) for k, v in zm.items()}},
-            "univariate_mh": {"min_bulk_ess": ess_mh, "seconds": t_mh, "ess_per_s": ess_mh / t_mh,
-                              "accept": float(acc_mh.mean()), "exact_evals": ev_mh},
-            "speedup_ess_per_s": (ess_su / t_su) / (ess_ex / t_ex),
-            "warmup_s": t_warm, "train_s": t_train,
-            "mean_diff_in_mcse_units": {k: float(v) for k, v in z.items()},
-            "locations": "resampled every iteration (cut posterior)" if cut else "fixed",
-            "note": "exact and surrogate HMC share the adapted step size and dense metric; the surrogate "
-                    "is trained on the warmup's exact evaluations; data: clustered synthetic events on a "
-                    "40x40 grid of 50 km counties over 1,200 days"}
+    out = {"n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
+           "draws_per_chain": draws, "training_pairs": int(X.shape[0]), "train_loss": loss,
+           **res,
+           "speedup_ess_per_s": res["surrogate"]["ess_per_s_vs_exact"],
+           # at large N, where the exact evaluations dominate the time, the
+           # ratio of exact evaluations per effective sample is the ESS/s ratio
+           "speedup_when_exact_evaluations_dominate": (res["exact"]["exact_evals_per_ess"] /
+                                                       res["surrogate"]["exact_evals_per_ess"]),
+           "warmup_s": t_warm, "train_s": t_train,
+           "cut_posterior_reference": ref,
+           "locations": "resampled every iteration (cut posterior)" if cut else "fixed",
+           "note": "all samplers share the exact-HMC warmup's step size and dense metric; the surrogate "
+                   "is trained on the warmup's exact evaluations; data: clustered synthetic events on a "
+                   "40x40 grid of 50 km counties over 1,200 days"}
+    return out
 
 
 def torch_device():
@@ -399,6 +390,11 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 30-chain batch measurement")
     ap.add_argument("--hmc-cut-reference", type=int, default=6,
                     help="location draws per chain for the independent cut-posterior reference (0: off)")
+    ap.add_argument("--hmc-only", action="store_true",
+                    help="run only the HMC comparison (cut scheme, exact vs surrogate) and print it")
+    ap.add_argument("--hmc-chains", type=int, default=4)
+    ap.add_argument("--hmc-warmup", type=int, default=300)
+    ap.add_argument("--hmc-draws", type=int, default=300)
     ap.add_argument("--hmc-n", type=int, default=50_000,
                     help="events for the HMC ESS/s comparison (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=4)
@@ -420,6 +416,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.hmc_only:
+        # one HMC comparison at a chosen size (exact vs surrogate, cut scheme,
+        # the exact underflow skip on: same results, less work)
+        torch.cuda.set_stream(torch.cuda.Stream())
+        r = bench_hmc(args.hmc_n, cut=True, chains=args.hmc_chains, warmup=args.hmc_warmup,
+                      draws=args.hmc_draws, lite=True, flags=HAWKES_SKIP_UNDERFLOW)
+        print(json.dumps({"hmc_only": r}))
+        return
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     # one dedicated stream for the library, the L2 flush and the timing events

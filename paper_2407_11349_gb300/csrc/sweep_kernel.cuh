@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 s_bad = 1;  // problem index out of range: do not read its descriptor
             } else if (MODE == MODE_BATCH && k < nitems) {
                 const ProbDesc d = probs[items[k].w];
-                vpd->rec = d.rec; vpd->lo = d.lo; vpd->hi = d.hi; vpd->tb = d.tb;
+                // every field the item reads (the times for the underflow skip)
+                vpd->t = d.t; vpd->rec = d.rec; vpd->lo = d.lo; vpd->hi = d.hi; vpd->tb = d.tb;
                 vpd->cc = d.cc; vpd->acc = d.acc; vpd->n = d.n; vpd->npad = d.npad;
             }
         }

@@ -62,10 +62,11 @@ class HawkesTarget:
     Each chain owns a context with the same events and its own resample
     stream; ``resample_eval`` draws new locations for every chain and then
     evaluates (one captured graph), ``eval`` evaluates at fixed locations.
-    Returns the log-likelihood and its gradient in eta = log p.
+    Returns the log-likelihood and its gradient in eta = log p.  ``flags``:
+    extra batch flags (model options, the exact underflow skip).
     """
 
-    def __init__(self, ds, n_chains, seed=0, device=0):
+    def __init__(self, ds, n_chains, seed=0, device=0, flags=0):
         import torch
 
         from .hawkes import HAWKES_F32, Batch, Hawkes, HawkesError
@@ -80,8 +81,8 @@ class HawkesTarget:
         self.dp = torch.zeros((n_chains, 6), dtype=torch.float64, device=f"cuda:{device}")
         self.dout = torch.zeros((n_chains, 7), dtype=torch.float64, device=f"cuda:{device}")
         self.host = torch.zeros((n_chains, 7), dtype=torch.float64).pin_memory()
-        self.b_rs = Batch(self.hks, [seed] * n_chains, list(range(n_chains)), HAWKES_F32, s)
-        self.b_ev = Batch(self.hks, None, None, HAWKES_F32, s)
+        self.b_rs = Batch(self.hks, [seed] * n_chains, list(range(n_chains)), HAWKES_F32 | flags, s)
+        self.b_ev = Batch(self.hks, None, None, HAWKES_F32 | flags, s)
         self.b_rs.capture(self.dp.data_ptr(), self.dout.data_ptr())
         self.b_ev.capture(self.dp.data_ptr(), self.dout.data_ptr())
         self.n_exact = 0

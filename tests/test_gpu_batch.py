@@ -158,3 +158,33 @@ def test_batch_tune_cached(problems, tmp_path):
             _close(got[p], *ref[p], f"cached configuration problem {p}")
     finally:
         b.close()
+
+
+def test_batch_with_underflow_skip(problems):
+    """The batch with the exact underflow skip (which reads each problem's
+    times from its descriptor) against sequential calls without it."""
+    from paper_2407_11349_gb300.hawkes import HAWKES_SKIP_UNDERFLOW
+    torch, dss, params, hks, seeds, streams = problems
+    assert max(ds.t[-1] - ds.t[0] for ds in dss) > 500.0  # long enough for skips
+    P = len(dss)
+    dp = torch.tensor(params, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+    b = Batch(hks, seeds, streams, HAWKES_F32 | HAWKES_SKIP_UNDERFLOW)
+    try:
+        torch.cuda.synchronize()
+        b.run(dp.data_ptr(), 11, dout.data_ptr())
+        b.wait()
+        got = dout.cpu().numpy()
+        ref = _sequential(hks, params, seeds, streams, 11)
+        for p in range(P):
+            _close(got[p], *ref[p], f"skip problem {p}")
+        b.capture(dp.data_ptr(), dout.data_ptr())
+        torch.cuda.synchronize()
+        b.run(dp.data_ptr(), 12, dout.data_ptr())
+        b.wait()
+        got = dout.cpu().numpy()
+        ref = _sequential(hks, params, seeds, streams, 12)
+        for p in range(P):
+            _close(got[p], *ref[p], f"skip graph problem {p}")
+    finally:
+        b.close()
