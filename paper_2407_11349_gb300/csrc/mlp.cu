@@ -114,6 +114,163 @@ __global__ void __launch_bounds__(128) k_gemm(const bf16* __restrict__ A, int ld
 }
 
 // ---------------------------------------------------------------------------
+// The same products on the 5th-generation tensor cores (tcgen05): one CTA of
+// 128 threads computes a 128 x 256 tile of C = A . Bt^T (every product here
+// has N = 256) with the FP32 accumulator in tensor memory.
+//   - K is staged in chunks of 64 BF16 values: the A rows [m0, m0 + 128) and
+//     all 256 Bt rows, as 8 x 16-byte core matrices in the unswizzled
+//     K-major layout: core matrix (row group i, K group j) at byte
+//     (8 i + j) * 128, so the K step between core matrices is 128 bytes and
+//     the row-group step 1024 bytes.  (Had the two offsets been read the
+//     other way round, every access would still fall inside the operand's
+//     buffer.)
+//   - One thread issues the four K = 16 products of a chunk and commits them
+//     to an mbarrier; the chunk's buffers are refilled after it completes.
+//   - Warp w reads TMEM lanes [32 w, 32 w + 32) (tile rows) 16 columns at a
+//     time for the epilogue.
+// A wait that gives up latches HAWKES_ERR_TIMEOUT in *err, skips the
+// epilogue, and the tensor memory is still released.
+// ---------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_N = 256, TC_KC = 64;
+constexpr uint32_t TC_BYTES_A = TC_M * TC_KC * 2, TC_BYTES_B = TC_N * TC_KC * 2;
+constexpr uint32_t TC_SMEM = TC_BYTES_A + TC_BYTES_B;
+// kind::f16 instruction descriptor: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((TC_N >> 3) << 17) |
+                              ((TC_M >> 4) << 24);
+
+constexpr uint32_t TC_LBO = 128, TC_SBO = (TC_KC / 8) * 128;  // K step, row-group step (bytes)
+
+__device__ __forceinline__ uint32_t core_off(int r, int j) {
+    return static_cast<uint32_t>(((r >> 3) * (TC_KC / 8) + j) * 128 + (r & 7) * 16);
+}
+
+// Shared-memory matrix descriptor: start, K-direction and row-group byte
+// offsets (all >> 4), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) |
+           (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(const bf16* __restrict__ A, int lda, int M,
+                                                    const bf16* __restrict__ Bt, int ldb, int K,
+                                                    Epi e, int ldc, int* err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M;
+    unsigned char* sA = tc_smem;
+    unsigned char* sB = tc_smem + TC_BYTES_A;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         hk::smem_u32(&s_tmem)),
+                     "r"(TC_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        hk::mbar_init(&bar, 1);
+        hk::fence_barrier_init();
+        s_fail = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    uint32_t phase = 0;
+    for (int k0 = 0; k0 < K && !s_fail; k0 += TC_KC) {
+        for (int idx = tid; idx < TC_M * 8; idx += 128) {  // 16-byte pieces of A
+            const int r = idx >> 3, j = idx & 7;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m0 + r < M)
+                v = *reinterpret_cast<const uint4*>(A + static_cast<size_t>(m0 + r) * lda + k0 + j * 8);
+            *reinterpret_cast<uint4*>(sA + core_off(r, j)) = v;
+        }
+        for (int idx = tid; idx < TC_N * 8; idx += 128) {  // and of Bt
+            const int r = idx >> 3, j = idx & 7;
+            *reinterpret_cast<uint4*>(sB + core_off(r, j)) =
+                *reinterpret_cast<const uint4*>(Bt + static_cast<size_t>(r) * ldb + k0 + j * 8);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int s4 = 0; s4 < TC_KC / 16; ++s4) {
+                // K = 16 values = core-matrix columns 2 s4 and 2 s4 + 1
+                const uint64_t da = smem_desc(hk::smem_u32(sA) + s4 * 2 * TC_LBO, TC_LBO, TC_SBO);
+                const uint64_t db = smem_desc(hk::smem_u32(sB) + s4 * 2 * TC_LBO, TC_LBO, TC_SBO);
+                const uint32_t accumulate = (k0 > 0 || s4 > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(TC_IDESC), "r"(accumulate)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             hk::smem_u32(&bar))
+                         : "memory");
+            if (!hk::mbar_wait(&bar, phase)) {
+                s_fail = 1;
+                atomicCAS(err, 0, HAWKES_ERR_TIMEOUT);
+            }
+        }
+        phase ^= 1u;
+        __syncthreads();
+    }
+    if (!s_fail) {
+        tc_fence_after();
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                  "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                  "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(tmem + (static_cast<uint32_t>(warp * 32) << 16) + static_cast<uint32_t>(c0)));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+                const size_t o = static_cast<size_t>(row) * ldc + c0;
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    v[q] = __uint_as_float(r[q]);
+                    if (EPI == EPI_FWD2) v[q] = tanhf(v[q] + e.bias[c0 + q]);
+                    if (EPI == EPI_BWD1) {
+                        const float h = e.h[o + q];
+                        v[q] = v[q] * (1.f - h * h);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 16; q += 4)
+                    *reinterpret_cast<float4*>(e.out + o + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+            }
+        }
+    } else if (tid == 0) {
+        (void)hk::mbar_wait(&bar, phase ^ 1u);  // bounded: let products in flight finish
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Small layers and reductions (FP32).
 // ---------------------------------------------------------------------------
 // h1 = tanh(x W1^T + b1): FP32 copy, BF16 row-major copy, BF16 transposed copy.
@@ -382,6 +539,7 @@ struct hawkes_mlp {
           *dZ2f = nullptr, *dZ1f = nullptr;
     bf16 *H1b = nullptr, *H1Tb = nullptr, *dZ2b = nullptr, *dZ2Tb = nullptr;
     double* hbuf = nullptr;  // pinned host scratch
+    int* err = nullptr;      // latched device error (a tensor-core wait that gave up)
 };
 
 namespace {
@@ -415,22 +573,34 @@ int alloc(T** p, size_t count) {
     return st_of(cudaMalloc(reinterpret_cast<void**>(p), (count ? count : 1) * sizeof(T)));
 }
 
+// Read and clear the latched device error (synchronous).
+int take_err(hawkes_mlp* m) {
+    HM_CUDA(cudaMemcpyAsync(m->hbuf + 63, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    HM_CUDA(cudaStreamSynchronize(m->stream));
+    int e = 0;
+    std::memcpy(&e, m->hbuf + 63, sizeof(int));
+    if (e != 0) HM_CUDA(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream));
+    return e;
+}
+
 // Forward (and, with targets, backward) of a batch already in m->X (and m->T).
 int forward_backward(hawkes_mlp* m, int B, bool train) {
     cudaStream_t st = m->stream;
     const int gH = (B * DH + 255) / 256, gO = (B * DOUT + 255) / 256;
     k_l1<<<gH, 256, 0, st>>>(m->X, m->P, B, m->H1f, m->H1b, m->H1Tb);
     Epi e2{m->P + OFF_B2, nullptr, m->H2f};
-    k_gemm<EPI_FWD2><<<dim3(DH / 64, B / 64), 128, 0, st>>>(m->H1b, DH, m->W2b, DH, DH, e2, DH);
+    const int gM = (B + TC_M - 1) / TC_M;
+    k_gemm_tc<EPI_FWD2><<<gM, 128, TC_SMEM, st>>>(m->H1b, DH, B, m->W2b, DH, DH, e2, DH, m->err);
     k_l3<<<gO, 256, 0, st>>>(m->H2f, m->P, B, train ? m->T : nullptr, m->Y, m->dY, m->loss);
     if (train) {
         k_bwd2<<<gH, 256, 0, st>>>(m->dY, m->H2f, m->P, B, m->dZ2f, m->dZ2b, m->dZ2Tb);
         k_grad_small<<<DOUT * DH + DOUT + DH, 256, 0, st>>>(m->dY, m->H2f, m->dZ2f, nullptr, m->X, B,
                                                             0, m->G);
         Epi ew{nullptr, nullptr, m->G + OFF_W2};
-        k_gemm<EPI_STORE><<<dim3(DH / 64, DH / 64), 128, 0, st>>>(m->dZ2Tb, B, m->H1Tb, B, B, ew, DH);
+        k_gemm_tc<EPI_STORE><<<DH / TC_M, 128, TC_SMEM, st>>>(m->dZ2Tb, B, DH, m->H1Tb, B, B, ew, DH,
+                                                             m->err);
         Epi eb{nullptr, m->H1f, m->dZ1f};
-        k_gemm<EPI_BWD1><<<dim3(DH / 64, B / 64), 128, 0, st>>>(m->dZ2b, DH, m->W2Tb, DH, DH, eb, DH);
+        k_gemm_tc<EPI_BWD1><<<gM, 128, TC_SMEM, st>>>(m->dZ2b, DH, B, m->W2Tb, DH, DH, eb, DH, m->err);
         k_grad_small<<<DH * DIN + DH, 256, 0, st>>>(nullptr, nullptr, nullptr, m->dZ1f, m->X, B, 1, m->G);
     }
     return st_of(cudaGetLastError());
@@ -472,6 +642,15 @@ int hawkes_mlp_create(hawkes_mlp** out, int device, void* cuda_stream, uint64_t 
             (rc = alloc(&m->dZ2b, BMAX * DH)) || (rc = alloc(&m->dZ2Tb, BMAX * DH)))
             break;
         if ((rc = st_of(cudaMallocHost(reinterpret_cast<void**>(&m->hbuf), 64 * sizeof(double))))) break;
+        if ((rc = alloc(&m->err, 1)) || (rc = st_of(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream))))
+            break;
+        for (const void* f : {reinterpret_cast<const void*>(k_gemm_tc<EPI_FWD2>),
+                              reinterpret_cast<const void*>(k_gemm_tc<EPI_STORE>),
+                              reinterpret_cast<const void*>(k_gemm_tc<EPI_BWD1>)})
+            if ((rc = st_of(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(TC_SMEM)))))
+                break;
+        if (rc) break;
         k_init_params<<<(NPARAMS + 255) / 256, 256, 0, m->stream>>>(m->P, seed);
         k_refresh_w2<<<DH * DH / 256, 256, 0, m->stream>>>(m->P, m->W2b, m->W2Tb);
         if ((rc = st_of(cudaMemsetAsync(m->M, 0, NPARAMS * sizeof(float), m->stream))) ||
@@ -497,7 +676,7 @@ void hawkes_mlp_destroy(hawkes_mlp* m) {
                     (void*)m->step, (void*)m->loss, (void*)m->stats, (void*)m->Xs, (void*)m->Ts,
                     (void*)m->X, (void*)m->T, (void*)m->H1f, (void*)m->H2f, (void*)m->Y, (void*)m->dY,
                     (void*)m->dZ2f, (void*)m->dZ1f, (void*)m->H1b, (void*)m->H1Tb, (void*)m->dZ2b,
-                    (void*)m->dZ2Tb})
+                    (void*)m->dZ2Tb, (void*)m->err})
         if (p) cudaFree(p);
     if (m->hbuf) cudaFreeHost(m->hbuf);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -576,7 +755,7 @@ int hawkes_mlp_train(hawkes_mlp* m, int64_t steps, int batch, double lr, uint64_
         HM_CUDA(cudaStreamSynchronize(m->stream));
         *last_loss = m->hbuf[0];
     }
-    return HAWKES_OK;
+    return take_err(m);
 }
 
 int hawkes_mlp_loss_grad(hawkes_mlp* m, int batch, const float* Xs, const float* Ts, double* loss,
@@ -594,7 +773,7 @@ int hawkes_mlp_loss_grad(hawkes_mlp* m, int batch, const float* Xs, const float*
     HM_CUDA(cudaMemcpyAsync(m->hbuf, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     HM_CUDA(cudaStreamSynchronize(st));
     if (loss) *loss = m->hbuf[0];
-    return HAWKES_OK;
+    return take_err(m);
 }
 
 int hawkes_mlp_predict(hawkes_mlp* m, int64_t count, const double* d_logp, double* d_out) {
@@ -625,7 +804,8 @@ int hawkes_mlp_wait(hawkes_mlp* m) {
     HK_NVTX("hawkes_mlp_wait");
     if (!m) return HAWKES_ERR_ARG;
     DeviceGuard g(m->device);
-    return st_of(cudaStreamSynchronize(m->stream));
+    HM_CUDA(cudaStreamSynchronize(m->stream));
+    return take_err(m);
 }
 
 }  // extern "C"
