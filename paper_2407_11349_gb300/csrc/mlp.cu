@@ -6,9 +6,9 @@
 // Inputs are the six standardised log-parameters and a constant 1; outputs
 // are the standardised log-likelihood and its six log-parameter partials.
 // Weights are kept in FP32 (Adam state and master copy); the 256 x 256 layer
-// runs on the tensor cores from BF16 copies of W2 and W2^T with BF16
-// activations and FP32 accumulation (mma.sync m16n8k16); the 7-wide layers
-// run in FP32.
+// runs on the 5th-generation tensor cores (tcgen05.mma, accumulator in tensor
+// memory) from BF16 copies of W2 and W2^T with BF16 activations and FP32
+// accumulation; the 7-wide layers run in FP32.
 //   forward:  h1 = tanh(x W1^T + b1), h2 = tanh(h1 W2^T + b2), y = h2 W3^T + b3
 //   loss:     mean over the batch and the 7 outputs of (y - t)^2
 #include <cuda_bf16.h>
@@ -30,9 +30,10 @@ static_assert(NPARAMS == HAWKES_MLP_NPARAMS, "parameter count");
 constexpr int BMAX = 4096;  // largest batch (a multiple of 64)
 
 // ---------------------------------------------------------------------------
-// Tensor-core GEMM: C[M x N] = A[M x K] . Bt[N x K]^T, BF16 in, FP32 accumulate.
-// A and Bt row-major; M, N multiples of 64, K a multiple of 16.  CTA tile
-// 64 x 64 (4 warps of 32 x 32, each 2 x 4 mma tiles of 16 x 8).
+// Epilogues of the 256 x 256 layer's products (C = A . Bt^T, FP32 out):
+//   EPI_FWD2  tanh(C + b2)            (forward, h2)
+//   EPI_STORE C                       (weight gradient of W2)
+//   EPI_BWD1  C * (1 - h1^2)          (backward through the first tanh)
 // ---------------------------------------------------------------------------
 enum { EPI_FWD2 = 0, EPI_STORE = 1, EPI_BWD1 = 2 };
 
@@ -42,81 +43,11 @@ struct Epi {
     float* out;         // [M x N] FP32
 };
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <int EPI>
-__global__ void __launch_bounds__(128) k_gemm(const bf16* __restrict__ A, int lda,
-                                              const bf16* __restrict__ Bt, int ldb, int K, Epi e,
-                                              int ldc) {
-    __shared__ __align__(16) bf16 sA[64][24];
-    __shared__ __align__(16) bf16 sB[64][24];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, t = lane & 3;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-    const int lr = tid >> 1, lc = (tid & 1) * 8;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        *reinterpret_cast<uint4*>(&sA[lr][lc]) =
-            *reinterpret_cast<const uint4*>(A + static_cast<size_t>(m0 + lr) * lda + k0 + lc);
-        *reinterpret_cast<uint4*>(&sB[lr][lc]) =
-            *reinterpret_cast<const uint4*>(Bt + static_cast<size_t>(n0 + lr) * ldb + k0 + lc);
-        __syncthreads();
-        uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const int rb = wm * 32 + i * 16;
-            af[i][0] = *reinterpret_cast<const uint32_t*>(&sA[rb + g][t * 2]);
-            af[i][1] = *reinterpret_cast<const uint32_t*>(&sA[rb + g + 8][t * 2]);
-            af[i][2] = *reinterpret_cast<const uint32_t*>(&sA[rb + g][t * 2 + 8]);
-            af[i][3] = *reinterpret_cast<const uint32_t*>(&sA[rb + g + 8][t * 2 + 8]);
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int nb = wn * 32 + j * 8;
-            bfr[j][0] = *reinterpret_cast<const uint32_t*>(&sB[nb + g][t * 2]);
-            bfr[j][1] = *reinterpret_cast<const uint32_t*>(&sB[nb + g][t * 2 + 8]);
-        }
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-        __syncthreads();
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int m = m0 + wm * 32 + i * 16 + g + (q >= 2 ? 8 : 0);
-                const int n = n0 + wn * 32 + j * 8 + t * 2 + (q & 1);
-                const size_t o = static_cast<size_t>(m) * ldc + n;
-                float v = acc[i][j][q];
-                if (EPI == EPI_FWD2) v = tanhf(v + e.bias[n]);
-                if (EPI == EPI_BWD1) {
-                    const float h = e.h[o];
-                    v = v * (1.f - h * h);
-                }
-                e.out[o] = v;
-            }
-}
-
 // ---------------------------------------------------------------------------
-// The same products on the 5th-generation tensor cores (tcgen05): one CTA of
-// 128 threads computes a 128 x 256 tile of C = A . Bt^T (every product here
-// has N = 256) with the FP32 accumulator in tensor memory.
+// The products on the 5th-generation tensor cores (tcgen05): one CTA of 128
+// threads computes a 128 x 256 tile of C = A . Bt^T (A [M x K] and Bt
+// [256 x K] row-major BF16; every product here has N = 256, K a multiple of
+// 64) with the FP32 accumulator in tensor memory.
 //   - K is staged in chunks of 64 BF16 values: the A rows [m0, m0 + 128) and
 //     all 256 Bt rows, as 8 x 16-byte core matrices in the unswizzled
 //     K-major layout: core matrix (row group i, K group j) at byte
