@@ -352,10 +352,13 @@ int hawkes_batch_tune_cached(hawkes_batch* batch, const hawkes_params* d_params,
  * its method).  A 7 -> 256 -> 256 -> 7 multilayer perceptron with tanh hidden
  * units maps (six standardised log-parameters, 1) to the standardised
  * log-likelihood and its six log-parameter partials d ell / d log p_k.
- * Trained on the GPU by this library's kernels (BF16 tensor-core products
- * with FP32 accumulation for the 256 x 256 layer, FP32 elsewhere, Adam),
- * evaluated inside HMC leapfrog trajectories; the exact kernel keeps the
- * accept/reject step.
+ * Trained on the GPU by this library's kernels (BF16 products on the
+ * 5th-generation tensor cores with the FP32 accumulator in tensor memory for
+ * the 256 x 256 layer, FP32 elsewhere, Adam), evaluated inside HMC leapfrog
+ * trajectories; the exact kernel keeps the accept/reject step.  A bounded
+ * device wait of the tensor-core kernels that gives up is latched and
+ * returned (HAWKES_ERR_TIMEOUT) by the next hawkes_mlp_train,
+ * hawkes_mlp_loss_grad or hawkes_mlp_wait.
  *
  * Parameters, flattened (HAWKES_MLP_NPARAMS floats): W1[256 x 7], b1[256],
  * W2[256 x 256], b2[256], W3[7 x 256], b3[7], row-major.
