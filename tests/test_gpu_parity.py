@@ -359,3 +359,44 @@ def test_tune_cache_on_the_device(hk, tmp_path):
     v3, hit3 = hk.tune_cached(P0, path, flags=HAWKES_BG_TIME, reps=1)  # another key: a miss
     assert not hit3 and len(json.load(open(path))) == 2
     hk.set_variant(0)
+
+
+def _synthetic(n, seed, t=None, same_xy=False):
+    ds = small_grid(n, seed=seed)
+    if t is not None:
+        ds.t = np.full(n, float(t))
+    if same_xy:
+        ds.x = np.full(n, ds.x[0])
+        ds.y = np.full(n, ds.y[0])
+    return ds
+
+
+def _check_flags(hk, ds, p, fl=0, what=""):
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle.loglik_grad(ds.t, ds.x, ds.y, p, s=ds.s, rows=True, bg_time_only=bool(fl & HAWKES_BG_TIME))
+    for prec, tl, tg in ((HAWKES_F64, TOL_F64, TOL_F64), (HAWKES_F32, TOL_LL32, TOL_G32)):
+        ll, g = hk.loglik_grad(p, prec | fl)
+        assert_close(ll, g, ref, rows, tl, tg, f"{what} prec={prec}")
+    return ref, rows
+
+
+def test_all_events_at_one_instant(hk):
+    """Every pair is a tie: no background, no excitation, every rate clipped;
+    ell = N log(1e-40) - sum Lambda_i, and only the Lambda terms have a gradient."""
+    ds = _synthetic(3000, 50, t=37.5)
+    ref, rows = _check_flags(hk, ds, P0, what="one instant")
+    assert np.all(rows[:, 7] == np.log(1e-40))
+
+
+def test_all_events_at_one_location(hk):
+    """r = 0 for every pair: the spatial factors are at their maxima."""
+    ds = _synthetic(2500, 51, same_xy=True)
+    _check_flags(hk, ds, P0, what="one location")
+    _check_flags(hk, ds, P0, HAWKES_BG_TIME, what="one location, time-only background")
+
+
+@pytest.mark.parametrize("p", [(0.5, 0.05, 0.01, 0.3, 50.0, 0.01),     # tiny bandwidths: most terms underflow
+                               (0.5, 5e3, 1e3, 0.3, 1e-3, 5e2)])      # huge bandwidths: every pair counts
+def test_extreme_bandwidths(hk, p):
+    ds = small_grid(3000, seed=52)
+    _check_flags(hk, ds, p, what=f"p={p}")
