@@ -92,7 +92,23 @@ enum {
      * Without this flag the background is the space-time Gaussian
      * mu phi2(r; tau_x) phi1(dt; tau_t).  Combines with every other flag.
      */
-    HAWKES_BG_TIME = 8
+    HAWKES_BG_TIME = 8,
+    /*
+     * FP32 path, whole sum only (no row window), space-time background:
+     * evaluate only the pairs that can be nonzero in FP32.  Events are
+     * ordered by location (a Morton curve) inside time windows cut between
+     * distinct times (hawkes_set_spatial_window); tiles of 256 events in that
+     * order whose every background and excitation term is provably an exact
+     * FP32 zero against a tile of rows (by bounding boxes of the current
+     * locations and time ranges, with 2 units of margin on each base-2
+     * exponent) are skipped.  The rest is evaluated pair by pair with exact
+     * tie and causality indicators, so the result is the full sum up to
+     * FP32 summation order.  The first call after hawkes_set_events builds
+     * the order on the host (synchronous: make it outside stream capture).
+     * Not for batches, HAWKES_F64, HAWKES_BG_TIME or row windows
+     * (HAWKES_ERR_ARG).
+     */
+    HAWKES_SKIP_SPATIAL = 16
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -441,6 +457,14 @@ int hawkes_check_bounded_wait(hawkes_ctx* ctx, double* seconds);
  *   hook; evaluations use the altered list until the next
  *   hawkes_set_events or hawkes_set_sweep_variant rebuilds it.
  */
+/*
+ * Events per time window of the HAWKES_SKIP_SPATIAL order (>= 256; default
+ * 32,768).  Longer windows make tiles more compact in space and skip more
+ * pairs, at the cost of a wider time span per tile.  Takes effect at the
+ * next evaluation with the flag.
+ */
+int hawkes_set_spatial_window(hawkes_ctx* ctx, int64_t events);
+
 int hawkes_debug_build(void);
 int hawkes_debug_set_item(hawkes_ctx* ctx, int k, int row_tile, int col_begin, int col_end);
 

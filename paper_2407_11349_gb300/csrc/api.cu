@@ -34,6 +34,12 @@ int sweep_num_variants();
 int sweep_blocks_per_sm(int v);
 std::vector<int4> sweep_items(int64_t n, int v);
 cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt);
+// sweep_spatial.cu
+int spatial_build(hawkes_ctx* c);
+cudaError_t spatial_launch(hawkes_ctx* c, int model1);
+void spatial_free(hawkes_ctx* c);
+int spatial_set_window(hawkes_ctx* c, int64_t window);
+void spatial_invalidate(hawkes_ctx* c);
 }  // namespace hk
 
 using namespace hk;
@@ -168,16 +174,26 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
     const bool f64 = (flags & HAWKES_F64) != 0;
     const int model = static_cast<int>(flags & (HAWKES_MODEL1 | HAWKES_BG_TIME));
     const bool bgt = (flags & HAWKES_BG_TIME) != 0;
-    const int skip = (!f64 && (flags & HAWKES_SKIP_UNDERFLOW)) ? 1 : 0;
+    const bool spatial = (flags & HAWKES_SKIP_SPATIAL) != 0;
+    if (spatial && (f64 || bgt || rb != 0 || re != c->n)) return HAWKES_ERR_ARG;
+    if (spatial) HK_TRY(spatial_build(c));  // synchronous on first use after set_events
+    const int skip = (!f64 && !spatial && (flags & HAWKES_SKIP_UNDERFLOW)) ? 1 : 0;
     const int prep_grid = grid_for(c, c->npad);
     HK_TRY(timed(c, HAWKES_K_PREP, [&] {
         k_prep<<<prep_grid, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->tb, d_params, model,
-                                                  f64 ? 0 : 1, skip, c->n, c->npad, c->rec, c->acc,
-                                                  c->cc, c->ctr, c->fix7);
+                                                  (f64 || spatial) ? 0 : 1, skip, c->n, c->npad, c->rec,
+                                                  c->acc, c->cc, c->ctr, c->fix7);
     }));
     if (!f64) {
         const bool sym = (rb == 0 && re == c->n);
-        HK_TRY(timed(c, HAWKES_K_SWEEP, [&] { launch_sweep(c, sym, rb, re, bgt); }));
+        cudaError_t se = cudaSuccess;
+        HK_TRY(timed(c, HAWKES_K_SWEEP, [&] {
+            if (spatial)
+                se = spatial_launch(c, (flags & HAWKES_MODEL1) ? 1 : 0);
+            else
+                launch_sweep(c, sym, rb, re, bgt);
+        }));
+        HK_CUDA(se);
         HK_TRY(timed(c, HAWKES_K_FINAL, [&] {
             k_finalize<<<c->final_blocks, 256, 0, c->stream>>>(c->acc, c->t, c->cc, c->npad, rb, re, 1,
                                                                c->fixlist, c->ctr, c->partials,
@@ -328,6 +344,7 @@ void hawkes_destroy(hawkes_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_events(c);
     free_counties(c);
+    spatial_free(c);
     dfree(c->ctr); dfree(c->cc); dfree(c->params_dev); dfree(c->out_dev); dfree(c->fix7);
     dfree(c->partials);
     if (c->out_host) cudaFreeHost(c->out_host);
@@ -392,6 +409,7 @@ int hawkes_set_events(hawkes_ctx* c, int64_t n, const double* t, const double* x
     c->items_variant = -1;
     rc = ensure_items(c);
     if (rc != HAWKES_OK) return fail(rc);
+    spatial_invalidate(c);  // the spatial order is rebuilt on its next use
     return HAWKES_OK;
 }
 
@@ -533,7 +551,8 @@ int hawkes_tune(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, int reps,
     HK_NVTX("hawkes_tune");
     if (!c || !p || reps < 1) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
-    if (!params_ok(p) || (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64))) != 0)
+    if (!params_ok(p) ||
+        (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64 | HAWKES_SKIP_SPATIAL))) != 0)
         return HAWKES_ERR_ARG;
     DeviceGuard g(c->device);
     const bool prof = c->prof;
@@ -596,7 +615,8 @@ int hawkes_tune_cached(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, in
     using namespace hk;
     if (!c || !p || reps < 1 || !cache_path) return HAWKES_ERR_ARG;
     if (c->n == 0) return HAWKES_ERR_STATE;
-    if (!params_ok(p) || (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64))) != 0)
+    if (!params_ok(p) ||
+        (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64 | HAWKES_SKIP_SPATIAL))) != 0)
         return HAWKES_ERR_ARG;
     DeviceGuard g(c->device);
     const std::string dk = device_key();
@@ -629,4 +649,10 @@ int hawkes_debug_set_item(hawkes_ctx* c, int k, int row_tile, int col_begin, int
     HK_CUDA(cudaMemcpy(c->items + k, &it, sizeof(int4), cudaMemcpyHostToDevice));
     c->items_variant = -1;  // rebuilt by the next variant selection or event set
     return HAWKES_OK;
+}
+
+int hawkes_set_spatial_window(hawkes_ctx* c, int64_t events) {
+    HK_NVTX("hawkes_set_spatial_window");
+    if (!c || events < TC) return HAWKES_ERR_ARG;
+    return spatial_set_window(c, events);
 }

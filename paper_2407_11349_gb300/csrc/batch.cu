@@ -188,7 +188,7 @@ int hawkes_batch_create(hawkes_batch** out, hawkes_ctx* const* problems, int32_t
     if (!out) return HAWKES_ERR_ARG;
     *out = nullptr;
     if (!problems || n_problems < 1 ||
-        (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64))) != 0 ||
+        (flags & ~(kFlagsAll & ~static_cast<uint32_t>(HAWKES_F64 | HAWKES_SKIP_SPATIAL))) != 0 ||
         (seeds == nullptr) != (streams == nullptr))
         return HAWKES_ERR_ARG;
     const int dev = problems[0] ? problems[0]->device : -1;

@@ -44,7 +44,10 @@ constexpr bool kDebug = false;
 inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
 // Every flag bit the log-likelihood calls accept.
-constexpr uint32_t kFlagsAll = HAWKES_F64 | HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW | HAWKES_BG_TIME;
+constexpr uint32_t kFlagsAll =
+    HAWKES_F64 | HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW | HAWKES_BG_TIME | HAWKES_SKIP_SPATIAL;
+
+struct SpatialState;  // the spatial-skip order of a context (sweep_spatial.cu)
 
 constexpr int WARPS = 8;
 constexpr int THREADS = WARPS * 32;
@@ -261,4 +264,6 @@ struct hawkes_ctx {
     bool prof = false;
     cudaEvent_t pev[2] = {nullptr, nullptr};
     hawkes_profile pacc{};
+
+    hk::SpatialState* sp = nullptr;  // HAWKES_SKIP_SPATIAL order (built on first use)
 };

@@ -27,6 +27,7 @@ HAWKES_MODEL2 = 0
 HAWKES_MODEL1 = 2
 HAWKES_SKIP_UNDERFLOW = 4
 HAWKES_BG_TIME = 8
+HAWKES_SKIP_SPATIAL = 16
 KERNEL_CLASSES = ("prep", "sweep", "rows64", "final", "reduce", "resample", "other")
 
 
@@ -67,6 +68,7 @@ _SIGS = {
     "hawkes_num_events": (ctypes.c_int64, [_VP]),
     "hawkes_sweep_variants": (ctypes.c_int, []),
     "hawkes_check_bounded_wait": (ctypes.c_int, [_VP, _D]),
+    "hawkes_set_spatial_window": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "hawkes_debug_build": (ctypes.c_int, []),
     "hawkes_debug_set_item": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "hawkes_set_sweep_variant": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -526,6 +528,10 @@ class Hawkes:
 
     def tune_cached(self, params, cache_path, flags=HAWKES_F32, reps=2):
         return hawkes_tune_cached(self.ctx, params, cache_path, flags, reps)
+
+    def set_spatial_window(self, events):
+        """Events per time window of the HAWKES_SKIP_SPATIAL order."""
+        _check(lib().hawkes_set_spatial_window(self.ctx, int(events)), "hawkes_set_spatial_window")
 
     def set_variant(self, v):
         hawkes_set_sweep_variant(self.ctx, v)

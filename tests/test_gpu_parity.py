@@ -400,3 +400,67 @@ def test_all_events_at_one_location(hk):
 def test_extreme_bandwidths(hk, p):
     ds = small_grid(3000, seed=52)
     _check_flags(hk, ds, p, what=f"p={p}")
+
+
+# ---------------------------------------------------------------------------
+# Exact spatial skip (HAWKES_SKIP_SPATIAL)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,window,ties,model1", [(300, 256, False, False), (6000, 1024, False, False),
+                                                  (6000, 1024, True, False), (5000, 256, False, True),
+                                                  (7000, 32768, True, False)])
+def test_spatial_skip_matches_oracle(hk, n, window, ties, model1):
+    """Events over 1,200 days on a 20 x 20 grid of 50 km counties: most pairs
+    are exact FP32 zeros by time or distance and are skipped; the sum of the
+    rest equals the oracle's at the FP32-path tolerances."""
+    from paper_2407_11349_gb300.hawkes import HAWKES_SKIP_SPATIAL
+    ds = synth.grid_dataset(n, 1200.0, 20, 20, seed=60 + n + window)
+    if ties:
+        ds = synth.integer_day_times(ds)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    hk.set_spatial_window(window)
+    s = None if model1 else ds.s
+    ref, rows = oracle.loglik_grad(ds.t, ds.x, ds.y, P0, s=s, rows=True)
+    fl = HAWKES_F32 | HAWKES_SKIP_SPATIAL | (HAWKES_MODEL1 if model1 else 0)
+    ll, g = hk.loglik_grad(P0, fl)
+    assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, f"spatial n={n} window={window}")
+    ll2, g2 = hk.loglik_grad((2.0, 5.0, 2.0, 0.9, 1.5, 0.7), fl)  # other bandwidths, same order
+    ref2, rows2 = oracle.loglik_grad(ds.t, ds.x, ds.y, (2.0, 5.0, 2.0, 0.9, 1.5, 0.7), s=s, rows=True)
+    assert_close(ll2, g2, ref2, rows2, TOL_LL32, TOL_G32, f"spatial n={n} other parameters")
+
+
+def test_spatial_skip_after_resample_and_at_100k(hk):
+    """The order is built from the locations of its first use; after a
+    resample the tiles' boxes follow the events.  N = 100,000 over 1,200 days
+    against the regular FP32 path."""
+    from paper_2407_11349_gb300.hawkes import HAWKES_SKIP_SPATIAL
+    ds = synth.config_dataset("c2")
+    hk.load(ds)
+    hk.set_spatial_window(32768)
+    ll_a, g_a = hk.loglik_grad(P0, HAWKES_F32 | HAWKES_SKIP_SPATIAL)
+    ll_b, g_b = hk.loglik_grad(P0, HAWKES_F32)
+    scale = np.abs(g_b) + 1e-3 * np.max(np.abs(g_b))
+    assert abs(ll_a - ll_b) <= 1e-6 * abs(ll_b) and np.all(np.abs(g_a - g_b) <= 1e-5 * scale)
+    hk.resample(3, 0, 1)
+    ll_a, g_a = hk.loglik_grad(P0, HAWKES_F32 | HAWKES_SKIP_SPATIAL)
+    ll_b, g_b = hk.loglik_grad(P0, HAWKES_F32)
+    scale = np.abs(g_b) + 1e-3 * np.max(np.abs(g_b))
+    assert abs(ll_a - ll_b) <= 1e-6 * abs(ll_b) and np.all(np.abs(g_a - g_b) <= 1e-5 * scale)
+
+
+def test_spatial_skip_rejects_what_it_does_not_cover(hk):
+    from paper_2407_11349_gb300.hawkes import HAWKES_SKIP_SPATIAL
+    ds = small_grid(2000, seed=61)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    for fl, rows in ((HAWKES_F64 | HAWKES_SKIP_SPATIAL, None), (HAWKES_BG_TIME | HAWKES_SKIP_SPATIAL, None),
+                     (HAWKES_SKIP_SPATIAL, (100, 900))):
+        with pytest.raises(HawkesError) as e:
+            if rows:
+                hk.loglik_grad(P0, fl, *rows)
+            else:
+                hk.loglik_grad(P0, fl)
+        assert e.value.status == -1
+    with pytest.raises(HawkesError):
+        hk.set_spatial_window(100)
+    ll, g = hk.loglik_grad(P0, HAWKES_F32)  # still usable
+    assert np.isfinite(ll)
