@@ -533,7 +533,7 @@ def main():
                                                               np.maximum(np.abs(np.asarray(g_y)), 1e-300))),
                     "note": "only tile pairs whose terms can be nonzero in FP32 are evaluated "
                             "(HAWKES_SKIP_SPATIAL: events ordered by location inside time windows of "
-                            "32,768 events); same result up to FP32 summation order; not the headline"}
+                            "131,072 events); same result up to FP32 summation order; not the headline"}
 
     # the same step with eq. 2's time-only background (a model option, not the headline)
     bgt_ms = []

