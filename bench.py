@@ -392,6 +392,10 @@ def main():
                     help="location draws per chain for the independent cut-posterior reference (0: off)")
     ap.add_argument("--hmc-only", action="store_true",
                     help="run only the HMC comparison (cut scheme, exact vs surrogate) and print it")
+    ap.add_argument("--hmc-fixed", action="store_true",
+                    help="with --hmc-only: locations held fixed instead of the cut scheme")
+    ap.add_argument("--hmc-spatial", action="store_true",
+                    help="with --hmc-only: exact evaluations with the spatial skip (chain by chain)")
     ap.add_argument("--hmc-chains", type=int, default=4)
     ap.add_argument("--hmc-warmup", type=int, default=300)
     ap.add_argument("--hmc-draws", type=int, default=300)
@@ -418,11 +422,12 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if args.hmc_only:
-        # one HMC comparison at a chosen size (exact vs surrogate, cut scheme,
-        # the exact underflow skip on: same results, less work)
+        # one HMC comparison at a chosen size (exact vs surrogate; an exact
+        # skip of zero terms on: same results, less work)
         torch.cuda.set_stream(torch.cuda.Stream())
-        r = bench_hmc(args.hmc_n, cut=True, chains=args.hmc_chains, warmup=args.hmc_warmup,
-                      draws=args.hmc_draws, lite=True, flags=HAWKES_SKIP_UNDERFLOW)
+        r = bench_hmc(args.hmc_n, cut=not args.hmc_fixed, chains=args.hmc_chains, warmup=args.hmc_warmup,
+                      draws=args.hmc_draws, lite=True,
+                      flags=HAWKES_SKIP_SPATIAL if args.hmc_spatial else HAWKES_SKIP_UNDERFLOW)
         print(json.dumps({"hmc_only": r}))
         return
     if world > 1:

@@ -69,7 +69,7 @@ class HawkesTarget:
     def __init__(self, ds, n_chains, seed=0, device=0, flags=0):
         import torch
 
-        from .hawkes import HAWKES_F32, Batch, Hawkes, HawkesError
+        from .hawkes import HAWKES_F32, HAWKES_SKIP_SPATIAL, Batch, Hawkes, HawkesError
 
         self.torch = torch
         self.HawkesError = HawkesError
@@ -81,10 +81,15 @@ class HawkesTarget:
         self.dp = torch.zeros((n_chains, 6), dtype=torch.float64, device=f"cuda:{device}")
         self.dout = torch.zeros((n_chains, 7), dtype=torch.float64, device=f"cuda:{device}")
         self.host = torch.zeros((n_chains, 7), dtype=torch.float64).pin_memory()
-        self.b_rs = Batch(self.hks, [seed] * n_chains, list(range(n_chains)), HAWKES_F32 | flags, s)
-        self.b_ev = Batch(self.hks, None, None, HAWKES_F32 | flags, s)
-        self.b_rs.capture(self.dp.data_ptr(), self.dout.data_ptr())
-        self.b_ev.capture(self.dp.data_ptr(), self.dout.data_ptr())
+        self.flags = HAWKES_F32 | flags
+        self.seed = seed
+        # the spatial skip runs on single contexts: evaluate chain by chain
+        self.sequential = bool(flags & HAWKES_SKIP_SPATIAL)
+        if not self.sequential:
+            self.b_rs = Batch(self.hks, [seed] * n_chains, list(range(n_chains)), self.flags, s)
+            self.b_ev = Batch(self.hks, None, None, self.flags, s)
+            self.b_rs.capture(self.dp.data_ptr(), self.dout.data_ptr())
+            self.b_ev.capture(self.dp.data_ptr(), self.dout.data_ptr())
         self.n_exact = 0
         self.n_events = ds.n
 
@@ -108,15 +113,34 @@ class HawkesTarget:
         self.n_exact += self.C
         return out[:, 0], out[:, 1:] * p
 
+    def _run_sequential(self, eta, iteration, resample):
+        p = np.exp(np.asarray(eta, dtype=np.float64))
+        out = np.full((self.C, 7), np.nan)
+        for c, h in enumerate(self.hks):
+            try:
+                if resample:
+                    h.resample(self.seed, c, iteration)
+                ll, g = h.loglik_grad(p[c], self.flags)
+                out[c, 0], out[c, 1:] = ll, g
+            except self.HawkesError:
+                self.n_failed += 1
+        self.n_exact += self.C
+        return out[:, 0], out[:, 1:] * p
+
     def resample_eval(self, iteration, eta):
+        if self.sequential:
+            return self._run_sequential(eta, iteration, True)
         return self._run(self.b_rs, eta, iteration)
 
     def eval(self, eta):
+        if self.sequential:
+            return self._run_sequential(eta, 0, False)
         return self._run(self.b_ev, eta, 0)
 
     def close(self):
-        self.b_rs.close()
-        self.b_ev.close()
+        if not self.sequential:
+            self.b_rs.close()
+            self.b_ev.close()
         for h in self.hks:
             h.close()
 
