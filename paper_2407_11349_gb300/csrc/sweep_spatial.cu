@@ -338,6 +338,7 @@ struct SpArgs {
     const double* box;
     int64_t n, npad;
     int ntiles, nI, nch, model1;
+    int chunk;  // column tiles per item (<= SP_CH)
 };
 
 // Persistent sweep over items (row tile I of the spatial order x a chunk of
@@ -373,8 +374,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_sweep_sp(SpArgs a, int* __restri
         const int item = s_item;
         if (item >= nitems || s_abort) break;
         const int I = item / a.nch;
-        const int cb = (item % a.nch) * SP_CH;
-        const int cend = min(cb + SP_CH, a.ntiles);
+        const int cb = (item % a.nch) * a.chunk;
+        const int cend = min(cb + a.chunk, a.ntiles);
         // the CTA's rows: tiles 8 I .. 8 I + 7 of the order
         SpRange rows;
         rows.empty = true;
@@ -532,7 +533,13 @@ cudaError_t spatial_launch(hawkes_ctx* c, int model1) {
     a.tmeta = sp->tmeta; a.box = sp->box; a.n = c->n; a.npad = c->npad;
     a.ntiles = sp->ntiles;
     a.nI = static_cast<int>(c->npad / SP_TR);
-    a.nch = (sp->ntiles + SP_CH - 1) / SP_CH;
+    // column chunks of up to SP_CH tiles, halved until there are at least 4
+    // items per SM (smaller problems would otherwise leave SMs idle)
+    a.chunk = SP_CH;
+    while (a.chunk > 32 && static_cast<int64_t>(a.nI) * ((sp->ntiles + a.chunk - 1) / a.chunk) <
+                               4LL * c->sms)
+        a.chunk /= 2;
+    a.nch = (sp->ntiles + a.chunk - 1) / a.chunk;
     a.model1 = model1;
     const int nitems = a.nI * a.nch;
     const size_t smem = 2 * TC * sizeof(Rec);  // 32 KB: below the default dynamic limit
