@@ -56,3 +56,27 @@ def test_strerror(lib):
 def test_library_is_sm_103a():
     # the fat binary must carry sm_103a code: nvcc was asked for nothing else
     assert libbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _declared_arities():
+    """Parameter count of every function include/*.h declares."""
+    out = {}
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(hawkes_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src, flags=re.S):
+            args = m.group(2).strip()
+            out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """The ctypes binding passes exactly as many arguments as each C
+    declaration takes."""
+    from paper_2407_11349_gb300 import hawkes
+    arity = _declared_arities()
+    assert len(arity) >= 40
+    wrong = {n: (arity[n], len(hawkes._SIGS[n][1])) for n in arity
+             if n in hawkes._SIGS and arity[n] != len(hawkes._SIGS[n][1])}
+    assert not wrong, f"argument counts differ (header, binding): {wrong}"
