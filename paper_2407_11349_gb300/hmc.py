@@ -434,6 +434,17 @@ class MHSampler:
         for k in range(n):
             self.transition(adapt_rate=1.0 / np.sqrt(k + 1.0))
 
+    # ---- checkpoint -----------------------------------------------------
+    def state(self):
+        return {"kind": "mh", "q": self.q.copy(), "log_scale": self.log_scale.copy(),
+                "iteration": self.iteration, "rng": self.rng.bit_generator.state}
+
+    def set_state(self, st):
+        self.q = np.array(st["q"], dtype=np.float64)
+        self.log_scale = np.array(st["log_scale"], dtype=np.float64)
+        self.iteration = int(st["iteration"])
+        self.rng.bit_generator.state = st["rng"]
+
     def sample(self, n):
         out = np.zeros((self.C, n, 6))
         acc = np.zeros(n)
@@ -468,10 +479,15 @@ def cut_posterior_reference(target, prior, q_start, cov, eps, rounds, burn, draw
 
 
 def save(path, sampler, mlp=None, train_X=None, train_Y=None):
-    """Checkpoint the sampler (and the surrogate: weights + its training set,
-    from which its standardisation is recomputed) to an .npz file."""
+    """Checkpoint the sampler (HMC or univariate MH; and the surrogate:
+    weights + its training set, from which its standardisation is
+    recomputed) to an .npz file."""
     import json
     st = sampler.state()
+    if st.get("kind") == "mh":
+        np.savez(path, kind="mh", q=st["q"], log_scale=st["log_scale"], iteration=st["iteration"],
+                 rng=json.dumps(st["rng"]))
+        return
     extra = {}
     if mlp is not None:
         extra["mlp_params"] = mlp.get_params()
@@ -484,6 +500,10 @@ def save(path, sampler, mlp=None, train_X=None, train_Y=None):
 def load(path, sampler, mlp=None):
     import json
     z = np.load(path, allow_pickle=False)
+    if "kind" in z and str(z["kind"]) == "mh":
+        sampler.set_state({"q": z["q"], "log_scale": z["log_scale"], "iteration": int(z["iteration"]),
+                           "rng": json.loads(str(z["rng"]))})
+        return
     sampler.set_state({"q": z["q"], "eps": z["eps"], "cov": z["cov"], "iteration": int(z["iteration"]),
                        "L": int(z["L"]), "jitter": float(z["jitter"]), "rng": json.loads(str(z["rng"]))})
     if mlp is not None and "mlp_params" in z:

@@ -236,3 +236,16 @@ def test_cut_posterior_reference_matches_the_mixture_in_closed_form():
     assert np.all(np.abs(m_cr.mean(axis=0) - mean) < 4.5 * se), (m_cr.mean(axis=0), mean, se)
     pooled = d.reshape(-1, 6).var(axis=0)
     assert np.all(np.abs(pooled / var - 1) < 0.25), (pooled, var)
+
+
+def test_mh_checkpoint_resume_is_bit_identical(tmp_path):
+    C = 3
+    a = hmc.MHSampler(GaussTarget(M, S, C), hmc.Prior(ETA0), np.tile(M, (C, 1)), seed=11)
+    a.warmup(30)
+    path = tmp_path / "mh.npz"
+    hmc.save(path, a)
+    ref = [a.transition().copy() for _ in range(12)]
+    b = hmc.MHSampler(GaussTarget(M, S, C), hmc.Prior(ETA0), np.zeros((C, 6)), seed=0)
+    hmc.load(path, b)
+    got = [b.transition().copy() for _ in range(12)]
+    assert np.array_equal(np.stack(ref), np.stack(got)) and np.array_equal(a.q, b.q)
