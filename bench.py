@@ -37,6 +37,16 @@ WORKLOAD = "c3: N=1,000,000 events, 1,200 d, 3,143 Voronoi counties (4,500x2,800
 # excitation exponent 2, excitation moments 3.  The two-word coordinate split
 # (4 more) is overhead, not counted.
 ALG_FP32_OPS_PER_PAIR = 19
+# The same count as first estimated before the kernel existed: 5 for the
+# differences and r^2, 1 for dt^2, 4 for both exponent arguments, 7 for the row
+# moments, 3 for the column moments and about 4 for per-pair scaling and
+# selection.  The kernel needs none of those 4 (scales and masks are applied
+# per row or per tile, outside the pair loop) and forms the excitation
+# argument with one FMA, so 19 is the stricter count; both are reported.
+SURVEY_FP32_OPS_PER_PAIR = 24
+# log-likelihood only: the row moments SBr, SBt, SEt, SEq and the column
+# moments SBr, SBt are not formed (6 fewer)
+LL_FP32_OPS_PER_PAIR = 13
 FP32_LANES_PER_SM = 128
 
 
@@ -149,43 +159,52 @@ def bench_batch(ds_c3, steps, warmup):
     variant, chunk, order, tune_ms = b.tune(dp.data_ptr(), dout.data_ptr(), reps=1)
     b.capture(dp.data_ptr(), dout.data_ptr())
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    for k in range(warmup):
-        b.run(dp.data_ptr(), k, dout.data_ptr())
-    b.wait()
-    t_b = 0.0
-    for k in range(steps):
+    douts = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+
+    def batched(it):
         e0, e1 = ev(), ev()
         e0.record(stream)
-        b.run(dp.data_ptr(), 100 + k, dout.data_ptr())
+        b.run(dp.data_ptr(), it, dout.data_ptr())
         e1.record(stream)
         b.wait()
-        t_b += e0.elapsed_time(e1) / 1000.0
-    batch_out = dout.cpu().numpy()
-    # the same work as one call per problem (async entry point, same stream)
-    douts = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
-    t_s = 0.0
-    for k in range(-warmup, steps):  # the timed steps use the batch's iterations
+        return e0.elapsed_time(e1)
+
+    def sequential(it):  # the same work as one call per problem (async entry point, same stream)
         e0, e1 = ev(), ev()
         e0.record(stream)
         for p in range(P):
-            hks[p].resample(seeds[p], streams[p], 100 + k)
+            hks[p].resample(seeds[p], streams[p], it)
             hks[p].loglik_grad_async(dp[p].data_ptr(), douts[p].data_ptr())
         e1.record(stream)
         torch.cuda.synchronize()
-        if k >= 0:
-            t_s += e0.elapsed_time(e1) / 1000.0
-    seq_last = douts.cpu().numpy()
+        return e0.elapsed_time(e1)
+
+    for k in range(warmup):
+        batched(k)
+        sequential(k)
+    # alternate the two so that drift of the clock or the L2 state hits both
+    tb, ts = [], []
+    for k in range(steps):
+        tb.append(batched(100 + k))
+        ts.append(sequential(100 + k))
+    batch_out, seq_last = dout.cpu().numpy(), douts.cpu().numpy()
     agree = float(np.max(np.abs(seq_last[:, 0] - batch_out[:, 0]) / np.abs(seq_last[:, 0])))
     b.close()
     for h in hks:
         h.close()
-    return {"value": steps * pairs / t_b, "unit": UNIT, "sequential_value": steps * pairs / t_s,
-            "speedup_vs_sequential": t_s / t_b, "ms_per_step": 1000 * t_b / steps,
-            "sequential_ms_per_step": 1000 * t_s / steps, "problems": P, "pairs_per_step": pairs,
+    ratios = sorted(s_ / b_ for s_, b_ in zip(ts, tb))
+    mb, ms_ = statistics.median(tb), statistics.median(ts)
+    return {"value": pairs / (mb / 1000.0), "unit": UNIT, "sequential_value": pairs / (ms_ / 1000.0),
+            "speedup_vs_sequential": ms_ / mb, "speedup_per_repeat": [round(r, 4) for r in ratios],
+            "speedup_min": ratios[0], "speedup_max": ratios[-1], "repeats": steps,
+            "ms_per_step": mb, "ms_per_step_all": [round(v, 2) for v in tb],
+            "sequential_ms_per_step": ms_, "sequential_ms_all": [round(v, 2) for v in ts],
+            "problems": P, "pairs_per_step": pairs,
             "tuned": {"variant": variant, "chunk_tiles": chunk, "order": order, "sweep_ms": tune_ms},
             "graph": True, "loglik_rel_diff_batch_vs_sequential": agree,
             "config": "30 chains x N=250,000 (own params, own resample stream) + 16 regional subsets "
-                      "N=5,000..200,000 (sum 899,416); one persistent launch in a CUDA graph"}
+                      "N=5,000..200,000 (sum 899,416); one persistent launch in a CUDA graph; "
+                      "medians of alternating batched / sequential repeats"}
 
 
 def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, ref_rounds=0,
@@ -306,6 +325,35 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     return out
 
 
+def accuracy_c3(hk, ds, p):
+    """The FP32 path's seven outputs on the c3 workload after resample(2, 0, 0)
+    against the oracle's values stored in tests/golden/oracle_c3.json (written
+    from the oracle alone), once the inputs are checked to be the same:
+    relative error of each output against itself, and against
+    max(|g_k|, 1e-3 sum_i |d ell_i / d p_k|) (the floor the parity tests use
+    for components that cancel)."""
+    from paper_2407_11349_gb300 import synth
+    path = os.path.join(ROOT, "tests", "golden", "oracle_c3.json")
+    if not os.path.exists(path):
+        return {"against": None, "note": "tests/golden/oracle_c3.json missing"}
+    doc = json.load(open(path))
+    hk.resample(2, 0, 0)
+    x, y = hk.locations()
+    if not synth.same_inputs(synth.fingerprint({"t": ds.t, "x": x, "y": y, "s": ds.s})["stats"],
+                             doc["inputs"]["stats"]):
+        return {"against": None, "note": "c3 inputs differ from the stored oracle's"}
+    ll, g = hk.loglik_grad(p, 0)
+    got = np.concatenate([[ll], g])
+    ref = np.asarray(doc["loglik_grad"])
+    raw = np.abs(got - ref) / np.abs(ref)
+    floor = np.maximum(np.abs(ref), 1e-3 * np.asarray(doc["abs_row_sums"]))
+    names = ["loglik", "d_mu", "d_tau_x", "d_tau_t", "d_theta", "d_omega", "d_h"]
+    return {"against": "FP64 oracle totals, tests/golden/oracle_c3.json (inputs fingerprint-matched)",
+            "rel_err": {k: float(v) for k, v in zip(names, raw)},
+            "rel_err_floored": {k: float(v) for k, v in zip(names, np.abs(got - ref) / floor)},
+            "targets": {"loglik": 1e-6, "grad": 1e-5}}
+
+
 def torch_device():
     import torch
     return torch.cuda.current_device()
@@ -402,6 +450,8 @@ def main():
     ap.add_argument("--hmc-n", type=int, default=50_000,
                     help="events for the HMC ESS/s comparison (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--batch-repeats", type=int, default=7,
+                    help="alternating batched / sequential repeats of the 30-chain batch")
     ap.add_argument("--variant", type=int, default=-1,
                     help="sweep kernel variant (default: autotuned)")
     ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3"],
@@ -414,8 +464,8 @@ def main():
     import torch.distributed as dist
 
     from paper_2407_11349_gb300 import synth
-    from paper_2407_11349_gb300.hawkes import (HAWKES_BG_TIME, HAWKES_F32, HAWKES_SKIP_SPATIAL,
-                                               HAWKES_SKIP_UNDERFLOW, Hawkes)
+    from paper_2407_11349_gb300.hawkes import (HAWKES_BG_TIME, HAWKES_F32, HAWKES_LOGLIK_ONLY,
+                                               HAWKES_SKIP_SPATIAL, HAWKES_SKIP_UNDERFLOW, Hawkes)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -557,6 +607,59 @@ def main():
                "note": "background mu phi1(dt; tau_t) / tau_x^2 (HAWKES_BG_TIME), same variant; "
                        "a model option, not the headline"}
 
+    # the same step evaluating the log-likelihood only (the paper's own
+    # computation, what its univariate Metropolis-Hastings sampler needs)
+    ll_ms = []
+    hk.profile(True)
+    for k in range(args.steps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        hk.resample(2, chain, 1300 + k)
+        ll_o, _ = hk.loglik_grad(p, HAWKES_F32 | HAWKES_LOGLIK_ONLY)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k:
+            ll_ms.append(e0.elapsed_time(e1))
+    pll = hk.profile(False)
+    hk.resample(2, chain, 1300 + args.steps)
+    ll_ref, _ = hk.loglik_grad(p, HAWKES_F32)
+    ll_sweep_s = pll["sweep"][1] / max(pll["sweep"][0], 1) / 1000.0
+    loglik_only = {"ms_per_step": sum(ll_ms) / len(ll_ms),
+                   "pairs_per_s": pairs / (sum(ll_ms) / len(ll_ms) / 1000.0),
+                   "sweep_ms": 1000 * ll_sweep_s,
+                   "roofline_frac": LL_FP32_OPS_PER_PAIR * pairs / ll_sweep_s / (
+                       torch.cuda.get_device_properties(local).multi_processor_count * FP32_LANES_PER_SM *
+                       float(peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6),
+                   "per_unit": f"{LL_FP32_OPS_PER_PAIR} FP32 lane ops per unordered pair",
+                   "loglik_rel_diff_vs_full": abs(ll_o - ll_ref) / abs(ll_ref),
+                   "note": "HAWKES_LOGLIK_ONLY: two moment sums per row instead of six, no gradient"}
+
+    # one evaluation split in row-tile shards that keep the symmetric sweep,
+    # against the row-window split without it (the split of Sec. 2.3.2), run
+    # one after another on this GPU; sweep kernel times only
+    shards = {}
+    dpar = torch.tensor(p, dtype=torch.float64, device="cuda")
+    mom = torch.empty(6 * n, dtype=torch.float64, device="cuda")
+    for G in (2, 4):
+        per = []
+        for gi in range(G):
+            hk.shard_moments(dpar.data_ptr(), gi, G, mom.data_ptr())  # builds the shard's list
+            hk.profile(True)
+            hk.shard_moments(dpar.data_ptr(), gi, G, mom.data_ptr())
+            per.append(hk.profile(False)["sweep"][1])
+        shards[f"symmetric_{G}_shard_sweep_ms"] = [round(v, 2) for v in per]
+    win = []
+    for a, b_ in ((0, n // 2), (n // 2, n)):
+        hk.profile(True)
+        hk.loglik_grad(p, HAWKES_F32, a, b_)
+        win.append(hk.profile(False)["sweep"][1])
+    shards["row_window_2_shard_sweep_ms"] = [round(v, 2) for v in win]
+    shards["whole_sweep_ms"] = round(1000 * sweep_avg_s, 2)
+    shards["note"] = ("sweep kernel time of each shard of one N=1M evaluation, run one after another on one "
+                      "GPU: symmetric row-tile shards (hawkes_shard_moments, equal pair counts) against "
+                      "uniform row windows evaluated without the symmetric shortcut")
+
     # end to end through the C ABI from pinned host buffers, every step
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory().numpy()
            for k, v in (("t", ds.t), ("x", ds.x), ("y", ds.y), ("county", ds.county.astype(np.int32)),
@@ -597,6 +700,7 @@ def main():
                          "kernel": f"k_sweep variant {variant} (FP32 pair sweep)",
                          "tuned_ms": [round(float(x), 3) for x in tune_ms],
                          "per_unit": f"{ALG_FP32_OPS_PER_PAIR} FP32 lane ops per unordered pair",
+                         "frac_at_24_ops_per_pair": SURVEY_FP32_OPS_PER_PAIR * pairs / sweep_avg_s / peak_ops,
                          "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
                                         f"(sm_max_mhz, {pk_src})",
                          "launch_ms": 1000 * sweep_avg_s},
@@ -604,14 +708,29 @@ def main():
             "skip_underflow": skip,
             "skip_spatial": skip_spatial,
             "bg_time": bg_time,
+            "loglik_only": loglik_only,
+            "shards": shards,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
         }
+        if args.workload == "c3":
+            acc = accuracy_c3(hk, ds, p)
+            out["accuracy"] = acc
+            if acc.get("rel_err"):
+                out["accuracy_loglik_rel_err"] = acc["rel_err"]["loglik"]
+                out["accuracy_grad_max_rel_err"] = max(v for k, v in acc["rel_err"].items() if k != "loglik")
+        out["loglik_only_ms_per_step"] = loglik_only["ms_per_step"]
+        out["skip_spatial_ms_per_step"] = skip_spatial["ms_per_step"]
         if world == 1 and not args.no_batch and args.workload == "c3":
-            out["batch30"] = bench_batch(ds, steps=3, warmup=1)
+            bt = bench_batch(ds, steps=args.batch_repeats, warmup=1)
+            out["batch30"] = bt
+            out["batch30_speedup"] = bt["speedup_vs_sequential"]
+            out["batch30_speedup_min_max"] = [bt["speedup_min"], bt["speedup_max"]]
         if world == 1 and args.hmc_n > 0 and args.workload == "c3":
             out["hmc"] = {"cut_posterior": bench_hmc(args.hmc_n, cut=True, ref_rounds=args.hmc_cut_reference),
                           "fixed_locations": bench_hmc(args.hmc_n, cut=False)}
+            out["hmc_cut_surrogate_ess_per_s_ratio"] = out["hmc"]["cut_posterior"]["speedup_ess_per_s"]
+            out["hmc_fixed_surrogate_ess_per_s_ratio"] = out["hmc"]["fixed_locations"]["speedup_ess_per_s"]
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ds)
         print(json.dumps(out))

@@ -69,7 +69,19 @@ enum {
 
 /* Flags for the log-likelihood calls. */
 enum {
-    HAWKES_F32 = 0,      /* pair terms in FP32 (SFU exp2), per-row and global sums in FP64 */
+    /*
+     * Pair terms in FP32 (SFU exp2), per-row and global sums in FP64.  FP32
+     * flushes every term below 2^-126 to zero.  Two FP64 fix-ups keep the
+     * result that of the exact sum: rows whose FP32 rate is within 10^9 n of
+     * that floor are recomputed in FP64 (so a flushed term cannot move a row
+     * across the 1e-40 clip), and a bound on what the flushed terms can move
+     * each output is kept per row; where an output's summed bound exceeds
+     * 1e-8 of its magnitude, the rows whose bound exceeds 1e-8 of that
+     * magnitude divided by the row count are recomputed in FP64 (at normal
+     * bandwidths none is; with bandwidths so small that every excitation
+     * term underflows, most are).
+     */
+    HAWKES_F32 = 0,
     HAWKES_F64 = 1,      /* every pair term in FP64 (slow on GB300: reference path) */
     HAWKES_MODEL2 = 0,   /* source bandwidth h * s_j from the county scale (eq. 3) */
     HAWKES_MODEL1 = 2,   /* s_j = 1 for every event (eq. 2) */
@@ -108,7 +120,16 @@ enum {
      * Not for batches, HAWKES_F64, HAWKES_BG_TIME or row windows
      * (HAWKES_ERR_ARG).
      */
-    HAWKES_SKIP_SPATIAL = 16
+    HAWKES_SKIP_SPATIAL = 16,
+    /*
+     * Evaluate the log-likelihood only (the paper's own computation, Sec.
+     * 2.3 and App. A; the univariate Metropolis-Hastings sampler of Sec. 2.2
+     * needs no gradient).  The FP32 sweep then forms two moment sums per row
+     * instead of six.  The six gradient outputs are NaN.  Combines with every
+     * other flag; with HAWKES_F64 or HAWKES_BG_TIME the full kernels run and
+     * only the gradient is dropped.
+     */
+    HAWKES_LOGLIK_ONLY = 32
 };
 
 /* Human-readable name of a status code (static storage). */
@@ -173,7 +194,8 @@ int hawkes_get_locations(hawkes_ctx* ctx, double* x, double* y);
  * the global t_N).  Pass row_begin = 0, row_end = n for the whole sum.
  *   params     host pointer
  *   flags      HAWKES_F32 or HAWKES_F64, | HAWKES_MODEL1 for s_j = 1,
- *              | HAWKES_SKIP_UNDERFLOW, | HAWKES_BG_TIME
+ *              | HAWKES_SKIP_UNDERFLOW, | HAWKES_BG_TIME, | HAWKES_SKIP_SPATIAL,
+ *              | HAWKES_LOGLIK_ONLY (grad then receives NaN)
  *   loglik     host pointer to one double (ell)
  *   grad       host pointer to six doubles, d ell / d (mu, tau_x, tau_t, theta, omega, h)
  * Synchronous: returns after the result is on the host.
@@ -198,6 +220,46 @@ int hawkes_loglik_grad_async(hawkes_ctx* ctx, const hawkes_params* d_params, uin
  */
 int hawkes_loglik_rows(hawkes_ctx* ctx, const hawkes_params* params, uint32_t flags,
                        double* out7, double* rows);
+
+/*
+ * Symmetric row-tile shards of one evaluation, for a split across GPUs (Sec.
+ * 2.3.2 splits the rows of one log-likelihood over GPUs and gathers the
+ * per-row results; this split keeps the sweep's symmetric shortcut, in which
+ * each unordered pair's background term is formed once and added to both of
+ * its rows).  Shard g of G sweeps the symmetric work list's row tiles
+ * [bounds[g], bounds[g+1]) (hawkes_shard_bounds with the context's
+ * hawkes_shard_tile_rows), which hold about 1/G of the pairs each.  A row's
+ * six moment sums then collect terms from every shard that holds a later row,
+ * so the ranks add their moment vectors (one all-reduce of 6 n doubles) and
+ * each finalises from the sum.
+ *
+ * hawkes_shard_bounds (host only; no device is touched): row boundaries
+ *   bounds[nshards + 1], bounds[0] = 0, bounds[nshards] = n, non-decreasing,
+ *   each inner one a multiple of tile_rows, chosen so that the shards' pair
+ *   counts (pairs (i, j < i) of their rows) are as equal as whole tiles allow.
+ *   Shards may be empty when nshards exceeds the tile count.
+ * hawkes_shard_tile_rows: rows per row tile of the context's sweep variant
+ *   (HAWKES_ERR_ARG for a NULL context).
+ * hawkes_shard_moments: queue shard `shard` of `nshards` and write its moment
+ *   sums to d_moments[6 n] (device, caller-owned; six consecutive vectors of
+ *   n doubles: SB, SBr, SBt, SE, SEt, SEq of every row, unnormalised, natural
+ *   units; rows outside the shard hold the column part it adds to them).
+ *   Flags as for hawkes_loglik_grad_async, FP32 path only (HAWKES_F64 and
+ *   HAWKES_SKIP_SPATIAL give HAWKES_ERR_ARG).  The first call for a new
+ *   (shard, nshards, sweep variant) builds that shard's work list
+ *   (synchronous: make it outside stream capture); later calls only queue.
+ * hawkes_finalize_moments: from d_moments[6 n] summed over all shards (device,
+ *   read when the work runs), queue the per-row finalisation and the global
+ *   reduction of the whole sum, and write ell and the six partials to d_out[7]
+ *   (device).  Same flags and parameters as the shards'.  Errors detected on
+ *   the device are latched in the context.
+ */
+int hawkes_shard_bounds(int64_t n, int64_t tile_rows, int nshards, int64_t* bounds);
+int64_t hawkes_shard_tile_rows(const hawkes_ctx* ctx);
+int hawkes_shard_moments(hawkes_ctx* ctx, const hawkes_params* d_params, uint32_t flags,
+                         int shard, int nshards, double* d_moments);
+int hawkes_finalize_moments(hawkes_ctx* ctx, const hawkes_params* d_params, uint32_t flags,
+                            const double* d_moments, double* d_out);
 
 /* Timing of the context's kernels, accumulated while profiling is on. */
 typedef struct {

@@ -1,5 +1,6 @@
 // C-ABI entry points of libhawkes (declared in include/hawkes.h): context and
 // buffer management, argument checks, and the launch sequence of each call.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -15,12 +16,16 @@ __global__ void k_setup(double*, double*, double*, const int32_t*, int32_t, cons
 __global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
                        const hawkes_params*, int, int, int, int64_t, int64_t, Rec*, double*, double*,
                        int*, double*);
-__global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
-                           int, int*, int*, double*, double*);
+__global__ void k_finalize(const double*, const double*, const int32_t*, const int32_t*,
+                           const double*, int64_t, int64_t, int64_t, int64_t, int, int*, int*,
+                           double*, double*);
+__global__ void k_flushfix(const double*, const double*, const double*, const double*,
+                           const double*, const int32_t*, const int32_t*, const double*, int,
+                           int64_t, int64_t, int64_t, int64_t, int*, double*, double*, double*);
 __global__ void k_rows64(const double*, const double*, const double*, const double*,
                          const int32_t*, const int32_t*, const double*, int, int64_t, int64_t,
                          int64_t, int64_t, int, const int*, int*, double*, double*, double*);
-__global__ void k_reduce(const double*, int, const double*, const double*, double*, int*);
+__global__ void k_reduce(const double*, int, const double*, double*, int64_t, double*, int*);
 __global__ void k_tri_area(const double*, int32_t, double*, int*);
 __global__ void k_tri_county(const int32_t*, int32_t, int32_t, double*, int32_t*, int32_t*, int*);
 __global__ void k_tri_check(const int32_t*, int32_t, int32_t, int*);
@@ -33,7 +38,10 @@ cudaError_t sweep_setup_attributes();
 int sweep_num_variants();
 int sweep_blocks_per_sm(int v);
 std::vector<int4> sweep_items(int64_t n, int v);
-cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt);
+cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt,
+                         bool ll);
+cudaError_t launch_sweep_list(hawkes_ctx* c, const int4* items, int nitems, bool bgt, bool ll);
+int sweep_variant_rows(int v);
 // sweep_spatial.cu
 int spatial_build(hawkes_ctx* c);
 cudaError_t spatial_launch(hawkes_ctx* c, int model1);
@@ -112,10 +120,17 @@ int grid_for(hawkes_ctx* c, int64_t items, int per_sm = 8) {
     return g < 1 ? 1 : static_cast<int>(g);
 }
 
+void drop_shard_items(hawkes_ctx* c) {
+    dfree(c->shard_items);
+    c->shard_nitems = 0;
+    c->shard_key[0] = c->shard_key[1] = c->shard_key[2] = -1;
+}
+
 void free_events(hawkes_ctx* c) {
     dfree(c->t); dfree(c->x); dfree(c->y); dfree(c->s); dfree(c->scale_c); dfree(c->county);
     dfree(c->lo); dfree(c->hi); dfree(c->tb); dfree(c->rec); dfree(c->acc); dfree(c->fixlist);
     dfree(c->items);
+    drop_shard_items(c);
     c->nitems = 0;
     c->items_variant = -1;
     dfree(c->rows9);
@@ -167,12 +182,39 @@ int select_variant(hawkes_ctx* c, int v) {
     return c->n ? ensure_items(c) : HAWKES_OK;
 }
 
+// Queue the FP32 path's finalisation of rows [rb, re) from the moment sums in
+// c->acc: per-row terms (rows near the FP32 floor recomputed in FP64), the
+// global reduction, and the FP64 recomputation of the rows whose flushed FP32
+// terms could matter to an output.
+int enqueue_finalize32(hawkes_ctx* c, int model, int64_t rb, int64_t re, double* d_out,
+                       double* d_rows9) {
+    HK_TRY(timed(c, HAWKES_K_FINAL, [&] {
+        k_finalize<<<c->final_blocks, 256, 0, c->stream>>>(c->acc, c->t, c->lo, c->hi, c->cc, c->n,
+                                                           c->npad, rb, re, 1, c->fixlist, c->ctr,
+                                                           c->partials, d_rows9);
+    }));
+    HK_TRY(timed(c, HAWKES_K_ROWS64, [&] {
+        k_rows64<<<c->sms, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model,
+                                                c->n, c->npad, 0, 0, 1, c->fixlist, c->ctr, c->acc,
+                                                c->fix7, d_rows9);
+    }));
+    HK_TRY(timed(c, HAWKES_K_REDUCE, [&] {
+        k_reduce<<<1, 256, 0, c->stream>>>(c->partials, c->final_blocks, c->fix7, c->cc, re - rb,
+                                           d_out, c->ctr);
+    }));
+    return timed(c, HAWKES_K_ROWS64, [&] {
+        k_flushfix<<<grid_for(c, re - rb, 2), 256, 0, c->stream>>>(
+            c->acc, c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model, c->n, c->npad, rb, re,
+            c->ctr, c->fix7, d_out, d_rows9);
+    });
+}
+
 // Queue one log-likelihood evaluation over rows [rb, re).  d_params: device
 // parameters; d_out: 7 doubles; d_rows9: optional per-row output [9 n].
 int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags, int64_t rb,
                    int64_t re, double* d_out, double* d_rows9) {
     const bool f64 = (flags & HAWKES_F64) != 0;
-    const int model = static_cast<int>(flags & (HAWKES_MODEL1 | HAWKES_BG_TIME));
+    const int model = static_cast<int>(flags & kModelBits);
     const bool bgt = (flags & HAWKES_BG_TIME) != 0;
     const bool spatial = (flags & HAWKES_SKIP_SPATIAL) != 0;
     if (spatial && (f64 || bgt || rb != 0 || re != c->n)) return HAWKES_ERR_ARG;
@@ -191,19 +233,10 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
             if (spatial)
                 se = spatial_launch(c, (flags & HAWKES_MODEL1) ? 1 : 0);
             else
-                launch_sweep(c, sym, rb, re, bgt);
+                launch_sweep(c, sym, rb, re, bgt, (flags & HAWKES_LOGLIK_ONLY) != 0);
         }));
         HK_CUDA(se);
-        HK_TRY(timed(c, HAWKES_K_FINAL, [&] {
-            k_finalize<<<c->final_blocks, 256, 0, c->stream>>>(c->acc, c->t, c->cc, c->npad, rb, re, 1,
-                                                               c->fixlist, c->ctr, c->partials,
-                                                               d_rows9);
-        }));
-        HK_TRY(timed(c, HAWKES_K_ROWS64, [&] {
-            k_rows64<<<c->sms, 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc,
-                                                    model, c->n, c->npad, 0, 0, 1, c->fixlist,
-                                                    c->ctr, c->acc, c->fix7, d_rows9);
-        }));
+        return enqueue_finalize32(c, model, rb, re, d_out, d_rows9);
     } else {
         const int64_t count = re - rb;
         int g = static_cast<int>(count < static_cast<int64_t>(c->sms) * 16 ? count : c->sms * 16);
@@ -214,14 +247,14 @@ int enqueue_loglik(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
                                                c->acc, c->fix7, d_rows9);
         }));
         HK_TRY(timed(c, HAWKES_K_FINAL, [&] {
-            k_finalize<<<c->final_blocks, 256, 0, c->stream>>>(c->acc, c->t, c->cc, c->npad, rb, re, 0,
-                                                               c->fixlist, c->ctr, c->partials,
-                                                               d_rows9);
+            k_finalize<<<c->final_blocks, 256, 0, c->stream>>>(c->acc, c->t, c->lo, c->hi, c->cc,
+                                                               c->n, c->npad, rb, re, 0, c->fixlist,
+                                                               c->ctr, c->partials, d_rows9);
         }));
     }
     HK_TRY(timed(c, HAWKES_K_REDUCE, [&] {
-        k_reduce<<<1, 256, 0, c->stream>>>(c->partials, c->final_blocks, c->fix7, c->cc, d_out,
-                                           c->ctr);
+        k_reduce<<<1, 256, 0, c->stream>>>(c->partials, c->final_blocks, c->fix7, c->cc, re - rb,
+                                           d_out, c->ctr);
     }));
     return HAWKES_OK;
 }
@@ -311,8 +344,9 @@ int hawkes_create(hawkes_ctx** out, int device, void* cuda_stream) {
         if ((rc = dalloc(&c->cc, CC_COUNT)) != HAWKES_OK) break;
         if ((rc = dalloc(&c->params_dev, 1)) != HAWKES_OK) break;
         if ((rc = dalloc(&c->out_dev, 8)) != HAWKES_OK) break;
-        if ((rc = dalloc(&c->fix7, 8)) != HAWKES_OK) break;
-        if ((rc = dalloc(&c->partials, static_cast<size_t>(8 * c->final_blocks))) != HAWKES_OK) break;
+        if ((rc = dalloc(&c->fix7, FIX_DOUBLES)) != HAWKES_OK) break;
+        if ((rc = dalloc(&c->partials, static_cast<size_t>(PART_STRIDE * c->final_blocks))) != HAWKES_OK)
+            break;
         if (cudaMallocHost(reinterpret_cast<void**>(&c->out_host), 8 * sizeof(double)) != cudaSuccess) {
             rc = HAWKES_ERR_OOM;
             break;
@@ -532,6 +566,101 @@ int hawkes_check_bounded_wait(hawkes_ctx* c, double* seconds) {
     if (seconds) *seconds = ms / 1000.0;
     const int err = take_device_error(c);
     return err == HAWKES_ERR_TIMEOUT ? HAWKES_OK : (err == HAWKES_OK ? HAWKES_ERR_STATE : err);
+}
+
+int hawkes_shard_bounds(int64_t n, int64_t tile_rows, int nshards, int64_t* bounds) {
+    if (n < 1 || tile_rows < 1 || nshards < 1 || !bounds) return HAWKES_ERR_ARG;
+    const int64_t nI = (n + tile_rows - 1) / tile_rows;
+    // pairs (i, j < i) of row tile I: sum of i over its rows [a, b)
+    std::vector<double> cum(static_cast<size_t>(nI) + 1, 0.0);
+    for (int64_t I = 0; I < nI; ++I) {
+        const int64_t a = I * tile_rows, b = std::min(a + tile_rows, n);
+        cum[I + 1] = cum[I] + static_cast<double>(b - a) * static_cast<double>(a + b - 1) / 2.0;
+    }
+    bounds[0] = 0;
+    int64_t k = 0;
+    for (int g = 1; g < nshards; ++g) {
+        const double target = cum[nI] * g / nshards;
+        while (k < nI && cum[k] < target) ++k;  // first tile boundary at or past the target
+        int64_t pick = k;
+        if (pick > 0 && target - cum[pick - 1] < cum[pick] - target) --pick;  // the nearer one
+        const int64_t b = std::min(pick * tile_rows, n);
+        bounds[g] = b > bounds[g - 1] ? b : bounds[g - 1];
+    }
+    bounds[nshards] = n;
+    return HAWKES_OK;
+}
+
+int64_t hawkes_shard_tile_rows(const hawkes_ctx* c) {
+    return c ? static_cast<int64_t>(sweep_variant_rows(c->variant)) : HAWKES_ERR_ARG;
+}
+
+int hawkes_shard_moments(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags, int shard,
+                         int nshards, double* d_moments) {
+    HK_NVTX("hawkes_shard_moments");
+    if (!c || !d_params || !d_moments || !aligned8(d_params) || !aligned8(d_moments))
+        return HAWKES_ERR_ARG;
+    if (nshards < 1 || shard < 0 || shard >= nshards) return HAWKES_ERR_ARG;
+    if ((flags & ~kFlagsAll) != 0 || (flags & (HAWKES_F64 | HAWKES_SKIP_SPATIAL)) != 0)
+        return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    DeviceGuard g(c->device);
+    const int key[3] = {nshards, shard, c->variant};
+    if (!(c->shard_items && key[0] == c->shard_key[0] && key[1] == c->shard_key[1] &&
+          key[2] == c->shard_key[2])) {
+        // this shard's row tiles of the symmetric work list (synchronous)
+        drop_shard_items(c);
+        const int64_t tr = sweep_variant_rows(c->variant);
+        std::vector<int64_t> b(static_cast<size_t>(nshards) + 1);
+        HK_TRY(hawkes_shard_bounds(c->n, tr, nshards, b.data()));
+        const int64_t I0 = b[shard] / tr, I1 = (b[shard + 1] + tr - 1) / tr;
+        std::vector<int4> mine;
+        for (const int4& it : sweep_items(c->n, c->variant))
+            if (it.x >= I0 && it.x < I1) mine.push_back(it);
+        HK_TRY(dalloc(&c->shard_items, mine.size()));
+        HK_CUDA(cudaMemcpyAsync(c->shard_items, mine.data(), mine.size() * sizeof(int4),
+                                cudaMemcpyHostToDevice, c->stream));
+        HK_CUDA(cudaStreamSynchronize(c->stream));
+        c->shard_nitems = static_cast<int>(mine.size());
+        for (int q = 0; q < 3; ++q) c->shard_key[q] = key[q];
+    }
+    const int model = static_cast<int>(flags & kModelBits);
+    const int skip = (flags & HAWKES_SKIP_UNDERFLOW) ? 1 : 0;
+    HK_TRY(timed(c, HAWKES_K_PREP, [&] {
+        k_prep<<<grid_for(c, c->npad), 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->tb, d_params,
+                                                            model, 1, skip, c->n, c->npad, c->rec,
+                                                            c->acc, c->cc, c->ctr, c->fix7);
+    }));
+    cudaError_t se = cudaSuccess;
+    HK_TRY(timed(c, HAWKES_K_SWEEP, [&] {
+        se = launch_sweep_list(c, c->shard_items, c->shard_nitems, (flags & HAWKES_BG_TIME) != 0,
+                               (flags & HAWKES_LOGLIK_ONLY) != 0);
+    }));
+    HK_CUDA(se);
+    HK_CUDA(cudaMemcpy2DAsync(d_moments, c->n * sizeof(double), c->acc, c->npad * sizeof(double),
+                              c->n * sizeof(double), 6, cudaMemcpyDeviceToDevice, c->stream));
+    return HAWKES_OK;
+}
+
+int hawkes_finalize_moments(hawkes_ctx* c, const hawkes_params* d_params, uint32_t flags,
+                            const double* d_moments, double* d_out) {
+    HK_NVTX("hawkes_finalize_moments");
+    if (!c || !d_params || !d_moments || !d_out || !aligned8(d_params) || !aligned8(d_moments) ||
+        !aligned8(d_out))
+        return HAWKES_ERR_ARG;
+    if ((flags & ~kFlagsAll) != 0 || (flags & (HAWKES_F64 | HAWKES_SKIP_SPATIAL)) != 0)
+        return HAWKES_ERR_ARG;
+    if (c->n == 0) return HAWKES_ERR_STATE;
+    DeviceGuard g(c->device);
+    const int model = static_cast<int>(flags & kModelBits);
+    HK_TRY(timed(c, HAWKES_K_PREP, [&] {  // constants and counters (nothing staged)
+        k_prep<<<grid_for(c, c->npad), 256, 0, c->stream>>>(c->t, c->x, c->y, c->s, c->tb, d_params,
+                                                            model, 0, 0, c->n, c->npad, c->rec,
+                                                            c->acc, c->cc, c->ctr, c->fix7);
+    }));
+    HK_CUDA(cudaMemcpy2DAsync(c->acc, c->npad * sizeof(double), d_moments, c->n * sizeof(double),
+                              c->n * sizeof(double), 6, cudaMemcpyDeviceToDevice, c->stream));
+    return enqueue_finalize32(c, model, 0, c->n, d_out, nullptr);
 }
 
 int hawkes_sweep_variants(void) { return sweep_num_variants(); }

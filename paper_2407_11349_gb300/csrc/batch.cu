@@ -15,12 +15,16 @@ namespace hk {
 __global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
                        const hawkes_params*, int, int, int, int64_t, int64_t, Rec*, double*, double*,
                        int*, double*);
-__global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
-                           int, int*, int*, double*, double*);
+__global__ void k_finalize(const double*, const double*, const int32_t*, const int32_t*,
+                           const double*, int64_t, int64_t, int64_t, int64_t, int, int*, int*,
+                           double*, double*);
+__global__ void k_flushfix(const double*, const double*, const double*, const double*,
+                           const double*, const int32_t*, const int32_t*, const double*, int,
+                           int64_t, int64_t, int64_t, int64_t, int*, double*, double*, double*);
 __global__ void k_rows64(const double*, const double*, const double*, const double*,
                          const int32_t*, const int32_t*, const double*, int, int64_t, int64_t,
                          int64_t, int64_t, int, const int*, int*, double*, double*, double*);
-__global__ void k_reduce(const double*, int, const double*, const double*, double*, int*);
+__global__ void k_reduce(const double*, int, const double*, double*, int64_t, double*, int*);
 __global__ void k_resample(const int32_t*, int64_t, const double*, const double*, const int32_t*,
                            const int32_t*, uint64_t, uint64_t, uint64_t, const uint64_t*, double*,
                            double*);
@@ -28,7 +32,8 @@ int sweep_num_variants();
 int sweep_blocks_per_sm(int v);
 std::vector<int4> sweep_items_batch(const std::vector<int64_t>& ns, int v, int chunk, int order);
 cudaError_t launch_sweep_batch(cudaStream_t st, int variant, int grid, const ProbDesc* probs,
-                               int nprobs, const int4* items, int nitems, int* ctr, bool bgt);
+                               int nprobs, const int4* items, int nitems, int* ctr, bool bgt,
+                               bool ll);
 
 __global__ void k_set_u64(uint64_t* dst, uint64_t v) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *dst = v;
@@ -126,7 +131,7 @@ int build_items(hawkes_batch* b, int variant, int chunk, int order) {
 // from b->d_iter by the resample kernels.
 int enqueue(hawkes_batch* b, const hawkes_params* d_params, double* d_out, bool time_sweep) {
     cudaStream_t st = b->stream;
-    const int model = static_cast<int>(b->flags & (HAWKES_MODEL1 | HAWKES_BG_TIME));
+    const int model = static_cast<int>(b->flags & kModelBits);
     const bool bgt = (b->flags & HAWKES_BG_TIME) != 0;
     const int skip = (b->flags & HAWKES_SKIP_UNDERFLOW) ? 1 : 0;
     const int P = static_cast<int>(b->probs.size());
@@ -143,18 +148,24 @@ int enqueue(hawkes_batch* b, const hawkes_params* d_params, double* d_out, bool 
     HB_CUDA(cudaMemsetAsync(b->d_ctr + CT_WORK, 0, sizeof(int), st));
     if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[0], st));
     HB_CUDA(launch_sweep_batch(st, b->variant, b->grid, b->d_probs, static_cast<int>(P), b->d_items,
-                               b->nitems, b->d_ctr,
-                               bgt));
+                               b->nitems, b->d_ctr, bgt,
+                               (b->flags & HAWKES_LOGLIK_ONLY) != 0));
     if (time_sweep) HB_CUDA(cudaEventRecord(b->ev[1], st));
     for (int p = 0; p < P; ++p) {
         hawkes_ctx* c = b->probs[p];
-        k_finalize<<<c->final_blocks, 256, 0, st>>>(c->acc, c->t, c->cc, c->npad, 0, c->n, 1,
-                                                    c->fixlist, c->ctr, c->partials, nullptr);
+        k_finalize<<<c->final_blocks, 256, 0, st>>>(c->acc, c->t, c->lo, c->hi, c->cc, c->n,
+                                                    c->npad, 0, c->n, 1, c->fixlist, c->ctr,
+                                                    c->partials, nullptr);
         k_rows64<<<b->sms, 256, 0, st>>>(c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model, c->n,
                                          c->npad, 0, 0, 1, c->fixlist, c->ctr, c->acc, c->fix7,
                                          nullptr);
-        k_reduce<<<1, 256, 0, st>>>(c->partials, c->final_blocks, c->fix7, c->cc, d_out + 7 * p,
-                                    c->ctr);
+        k_reduce<<<1, 256, 0, st>>>(c->partials, c->final_blocks, c->fix7, c->cc, c->n,
+                                    d_out + 7 * p, c->ctr);
+        int gf = static_cast<int>((c->n + 255) / 256);
+        if (gf > 2 * b->sms) gf = 2 * b->sms;
+        k_flushfix<<<gf, 256, 0, st>>>(c->acc, c->t, c->x, c->y, c->s, c->lo, c->hi, c->cc, model,
+                                       c->n, c->npad, 0, c->n, c->ctr, c->fix7, d_out + 7 * p,
+                                       nullptr);
     }
     HB_CUDA(cudaGetLastError());
     return HAWKES_OK;

@@ -44,8 +44,10 @@ constexpr bool kDebug = false;
 inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
 // Every flag bit the log-likelihood calls accept.
-constexpr uint32_t kFlagsAll =
-    HAWKES_F64 | HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW | HAWKES_BG_TIME | HAWKES_SKIP_SPATIAL;
+constexpr uint32_t kFlagsAll = HAWKES_F64 | HAWKES_MODEL1 | HAWKES_SKIP_UNDERFLOW | HAWKES_BG_TIME |
+                               HAWKES_SKIP_SPATIAL | HAWKES_LOGLIK_ONLY;
+// The flag bits that k_prep and the FP64 kernels read as the call's model.
+constexpr uint32_t kModelBits = HAWKES_MODEL1 | HAWKES_BG_TIME | HAWKES_LOGLIK_ONLY;
 
 struct SpatialState;  // the spatial-skip order of a context (sweep_spatial.cu)
 
@@ -119,8 +121,21 @@ enum {
     CC_SKIPDT,      // > 0: skip tiles whose smallest time gap (scaled) exceeds this
     CC_SKIPDTB,     // the background-only part of that bound (sqrt(128))
     CC_VALID,       // 1 if the parameters are valid
-    CC_COUNT
+    CC_CEMAX,       // max(0, max_j ce_j) of the call's model (0 for Model 1)
+    CC_BGT,         // 1 for the time-only background
+    CC_LLONLY,      // 1 when only the log-likelihood is evaluated
+    CC_FTHR,        // [7] flush-bound thresholds per output (< 0: nothing to recompute)
+    CC_COUNT = CC_FTHR + 7
 };
+
+// Per-block partials of k_finalize: the 7 outputs, then the 7 flush bounds.
+constexpr int PART_STRIDE = 16;
+// fix7 buffer: [0, 8) sums over rows recomputed because their rate is near the
+// FP32 floor, [8, 16) corrections of rows recomputed because of the flush bound.
+constexpr int FIX_DOUBLES = 16;
+// Relative share of an output's magnitude that the bound on the FP32 sweep's
+// flushed terms may reach before the rows that carry it are recomputed in FP64.
+constexpr double FLUSH_TAU = 1e-8;
 
 // Device counters.
 enum {
@@ -266,4 +281,10 @@ struct hawkes_ctx {
     hawkes_profile pacc{};
 
     hk::SpatialState* sp = nullptr;  // HAWKES_SKIP_SPATIAL order (built on first use)
+
+    // Work list of one shard of the symmetric sweep (hawkes_shard_moments),
+    // for (nshards, shard, variant) = shard_key; rebuilt when any changes.
+    int4* shard_items = nullptr;
+    int shard_nitems = 0;
+    int shard_key[3] = {-1, -1, -1};
 };

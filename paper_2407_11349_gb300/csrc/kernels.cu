@@ -98,7 +98,8 @@ __device__ __forceinline__ Consts make_consts(const hawkes_params* P, bool bg_ti
 }
 
 // Zero the accumulators, reset the counters and (FP32 path) stage the event table.
-// model: the HAWKES_MODEL1 and HAWKES_BG_TIME bits of the call's flags.
+// model: the HAWKES_MODEL1, HAWKES_BG_TIME and HAWKES_LOGLIK_ONLY bits of the
+// call's flags.
 // skip: evaluate only tiles whose terms can be nonzero in FP32 (see CC_SKIPDT).
 __global__ void k_prep(const double* __restrict__ t, const double* __restrict__ x,
                        const double* __restrict__ y, const double* __restrict__ s,
@@ -127,10 +128,14 @@ __global__ void k_prep(const double* __restrict__ t, const double* __restrict__ 
         cc[CC_SKIPDTB] = skip ? sqrt(128.0) : 0.0;
         cc[CC_SKIPDT] = skip ? fmax(sqrt(128.0), (cemax + 128.0) / k.omt) : 0.0;
         cc[CC_VALID] = k.valid ? 1.0 : 0.0;
+        cc[CC_CEMAX] = cemax;
+        cc[CC_BGT] = (model & HAWKES_BG_TIME) ? 1.0 : 0.0;
+        cc[CC_LLONLY] = (model & HAWKES_LOGLIK_ONLY) ? 1.0 : 0.0;
+        for (int q = 0; q < 7; ++q) cc[CC_FTHR + q] = -1.0;
         ctr[CT_WORK] = 0;
         ctr[CT_FIX] = 0;
         ctr[CT_DONE] = 0;
-        for (int q = 0; q < 8; ++q) fix7[q] = 0.0;
+        for (int q = 0; q < FIX_DOUBLES; ++q) fix7[q] = 0.0;
         if (!k.valid) set_error(ctr, HAWKES_ERR_ARG);
     }
     const double beta0 = (k.tx * k.tx) / (k.h * k.h);
@@ -179,6 +184,16 @@ __device__ void row_terms(const double* sums, double ti, const double* __restric
     const double lam = mu * SB + th * SE;
     double d[6] = {0, 0, 0, 0, 0, 0};
     double loglam;
+    if (cc[CC_LLONLY] != 0.0) {  // the sweep formed SB and SE only: no gradient
+        loglam = lam < CLIP ? log(CLIP) : log(lam);
+        const double a = (tN - ti) / tt, b = -ti / tt;
+        const double Lam = mu * (normcdf(a) - normcdf(b)) + th * (1.0 - exp(-om * (tN - ti)));
+        out[0] = loglam - Lam;
+        for (int q = 1; q < 7; ++q) out[q] = CUDART_NAN;
+        out[7] = loglam;
+        out[8] = Lam;
+        return;
+    }
     if (lam < CLIP) {
         loglam = log(CLIP);
     } else {
@@ -228,15 +243,69 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* dst)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Bound on what the FP32 sweep's flushed terms can move in a row.
+//
+// ex2.approx.ftz returns 0 for every term below 2^-126, and a product below
+// 2^-126 in an accumulation flushes too, so each FP32 moment sum of row i
+// lacks a nonnegative part that is at most (per source, natural units):
+//   SB  : F                         SE  : F
+//   SBr : F 126 / a_x               SEt : F max(t_i - t_1, 1 / sqrt(a_t))
+//   SBt : F 126 / a_t               SEq : F (ce_max + 127) 2 h^2 / log2(e)
+// with F = 2^-126 (plus margin for the approximation), summed over the row's
+// background sources (t_j != t_i) and excitation sources (t_j < t_i).  The
+// r^2 and dt^2 factors follow from 2^-a a <= 126 2^-126 for a >= 126; the
+// excitation's from 2^g (ce_max - g) <= 2^-126 (ce_max + 126) for g <= -126.
+// The row's outputs are N_k / lambda with N_k linear in the moments, so each
+// output moves by at most (|dN_k| + |N_k| dlambda / lambda) / lambda, and the
+// log-likelihood by dlambda / lambda.  A clipped row whose true rate could
+// reach the clip gets an infinite bound.
+// ---------------------------------------------------------------------------
+__device__ void row_flush_bound(const double* sums, double ti, double t1, int64_t nb, int64_t ne,
+                                const double* __restrict__ cc, double b[7]) {
+    constexpr double F = 1.2e-38;  // 2^-126 = 1.1755e-38, with margin
+    const double mu = cc[CC_MU], tx = cc[CC_TX], tt = cc[CC_TT];
+    const double th = cc[CC_TH], om = cc[CC_OM], h = cc[CC_H];
+    const double cB = cc[CC_CB], cE = cc[CC_CE];
+    const double fb = F * static_cast<double>(nb), fe = F * static_cast<double>(ne);
+    const double DB = cB * fb;
+    const double DBr = cc[CC_BGT] != 0.0 ? 0.0 : cB * fb * 126.0 * cc[CC_SR];
+    const double DBt = cB * fb * 126.0 * cc[CC_ST];
+    const double DE = cE * fe;
+    const double DEt = cE * fe * fmax(ti - t1, cc[CC_SET]);
+    const double DEq = cE * fe * (cc[CC_CEMAX] + 127.0) * cc[CC_SEQ];
+    const double SB = cB * sums[0], SBr = cB * sums[1], SBt = cB * sums[2];
+    const double SE = cE * sums[3], SEt = cE * sums[4], SEq = cE * sums[5];
+    const double lam = mu * SB + th * SE, dlam = mu * DB + th * DE;
+    if (lam < CLIP) {
+        const double inf = CUDART_INF;
+        for (int q = 0; q < 7; ++q) b[q] = (lam + dlam >= CLIP) ? inf : 0.0;
+        return;
+    }
+    const double il = 1.0 / lam, r = dlam * il;
+    const double N[6] = {SB, mu * (SBr / (tx * tx * tx) - 2.0 * SB / tx),
+                         mu * (SBt / (tt * tt * tt) - SB / tt), SE, th * (SE / om - SEt),
+                         th * (SEq / (h * h * h) - 2.0 * SE / h)};
+    const double dN[6] = {DB, mu * (DBr / (tx * tx * tx) + 2.0 * DB / tx),
+                          mu * (DBt / (tt * tt * tt) + DB / tt), DE, th * (DE / om + DEt),
+                          th * (DEq / (h * h * h) + 2.0 * DE / h)};
+    b[0] = r;
+    for (int q = 0; q < 6; ++q) b[1 + q] = (dN[q] + fabs(N[q]) * r) * il;
+}
+
 // Finalise rows [rb, re).  With `check` (FP32 sweep), rows whose rate could be
-// moved by FP32 underflow are queued for FP64 recomputation instead.
+// moved by FP32 underflow are queued for FP64 recomputation instead, and each
+// block's partials also carry the summed flush bounds of its other rows.
 __global__ void k_finalize(const double* __restrict__ acc, const double* __restrict__ t,
-                           const double* __restrict__ cc, int64_t npad, int64_t rb, int64_t re,
-                           int check, int* fixlist, int* ctr, double* partials, double* rows9) {
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+                           const int32_t* __restrict__ lo, const int32_t* __restrict__ hi,
+                           const double* __restrict__ cc, int64_t n, int64_t npad, int64_t rb,
+                           int64_t re, int check, int* fixlist, int* ctr, double* partials,
+                           double* rows9) {
+    double v[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const bool valid = cc[CC_VALID] != 0.0;
     const double thr = cc[CC_FLAGTHR];
     const double mu = cc[CC_MU], th = cc[CC_TH], cB = cc[CC_CB], cE = cc[CC_CE];
+    const double t1 = t[0];
     for (int64_t i = rb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; valid && i < re;
          i += (int64_t)gridDim.x * blockDim.x) {
         double sums[6];
@@ -258,10 +327,52 @@ __global__ void k_finalize(const double* __restrict__ acc, const double* __restr
         row_terms(sums, t[i], cc, o);
 #pragma unroll
         for (int q = 0; q < 7; ++q) v[q] += o[q];
+        if (check) {
+            double bd[7];
+            const int64_t l = lo[i];
+            row_flush_bound(sums, t[i], t1, l + (n - hi[i]), l, cc, bd);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) v[7 + q] += bd[q];
+        }
         if (rows9)
             for (int q = 0; q < 9; ++q) rows9[9 * i + q] = o[q];
     }
-    block_reduce_store<7>(v, partials + 8 * blockIdx.x);
+    block_reduce_store<14>(v, partials + PART_STRIDE * blockIdx.x);
+}
+
+// This thread's share (sources j = threadIdx.x + k blockDim.x) of row i's six
+// FP64 moment sums, in natural units: the pair terms of eqs. 2-3 written out.
+// ix2 = 1/(2 tau_x^2) (0 for the time-only background), it2 = 1/(2 tau_t^2),
+// ih2 = 1/(2 h^2).
+__device__ __forceinline__ void row_sums64(int64_t i, const double* __restrict__ t,
+                                           const double* __restrict__ x,
+                                           const double* __restrict__ y,
+                                           const double* __restrict__ s,
+                                           const int32_t* __restrict__ lo,
+                                           const int32_t* __restrict__ hi, bool model1, int64_t n,
+                                           double ix2, double it2, double ih2, double om,
+                                           double v[6]) {
+    const double ti = t[i], xi = x[i], yi = y[i];
+    const int64_t li = lo[i], hj = hi[i];
+    for (int q = 0; q < 6; ++q) v[q] = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double dt = ti - t[j], dx = xi - x[j], dy = yi - y[j];
+        const double r2 = dx * dx + dy * dy;
+        if (j < li || j >= hj) {
+            const double b = exp(-r2 * ix2 - dt * dt * it2);
+            v[0] += b;
+            v[1] += ix2 != 0.0 ? b * r2 : 0.0;
+            v[2] += b * dt * dt;
+        }
+        if (j < li) {
+            const double sj = model1 ? 1.0 : s[j];
+            const double is2 = 1.0 / (sj * sj);
+            const double e = is2 * exp(-om * dt - r2 * ih2 * is2);
+            v[3] += e;
+            v[4] += e * dt;
+            v[5] += e * r2 * is2;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -288,27 +399,9 @@ __global__ void k_rows64(const double* __restrict__ t, const double* __restrict_
             if (threadIdx.x == 0) set_error(ctr, HAWKES_ERR_BOUNDS);
             continue;  // uniform over the block: i depends on k only
         }
-        const double ti = t[i], xi = x[i], yi = y[i];
-        const int64_t li = lo[i], hj = hi[i];
-        double v[6] = {0, 0, 0, 0, 0, 0};
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-            const double dt = ti - t[j], dx = xi - x[j], dy = yi - y[j];
-            const double r2 = dx * dx + dy * dy;
-            if (j < li || j >= hj) {
-                const double b = exp(-r2 * ix2 - dt * dt * it2);
-                v[0] += b;
-                v[1] += ix2 != 0.0 ? b * r2 : 0.0;
-                v[2] += b * dt * dt;
-            }
-            if (j < li) {
-                const double sj = model1 ? 1.0 : s[j];
-                const double is2 = 1.0 / (sj * sj);
-                const double e = is2 * exp(-om * dt - r2 * ih2 * is2);
-                v[3] += e;
-                v[4] += e * dt;
-                v[5] += e * r2 * is2;
-            }
-        }
+        const double ti = t[i];
+        double v[6];
+        row_sums64(i, t, x, y, s, lo, hi, model1, n, ix2, it2, ih2, om, v);
         __shared__ double sums[8];
         block_reduce_store<6>(v, sums);
         __syncthreads();
@@ -328,25 +421,123 @@ __global__ void k_rows64(const double* __restrict__ t, const double* __restrict_
 }
 
 // Sum the per-block partials in a fixed order, add the FP64-recomputed rows,
-// write the 7 outputs.  One CTA.
+// write the 7 outputs.  One CTA.  The summed flush bounds of the FP32 sweep
+// (zero on the FP64 path) decide, per output, whether rows must be recomputed
+// by k_flushfix: when an output's bound exceeds FLUSH_TAU of its magnitude,
+// every row whose own bound exceeds FLUSH_TAU |output| / nrows is, so the rows
+// left in FP32 can move it by at most FLUSH_TAU of its magnitude.
 __global__ void k_reduce(const double* __restrict__ partials, int nparts,
-                         const double* __restrict__ fix7, const double* __restrict__ cc,
+                         const double* __restrict__ fix7, double* __restrict__ cc, int64_t nrows,
                          double* out, int* ctr) {
-    double v[7] = {0, 0, 0, 0, 0, 0, 0};
+    double v[14] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < nparts; b += blockDim.x)
-        for (int q = 0; q < 7; ++q) v[q] += partials[8 * b + q];
-    __shared__ double tot[8];
-    block_reduce_store<7>(v, tot);
+        for (int q = 0; q < 14; ++q) v[q] += partials[PART_STRIDE * b + q];
+    __shared__ double tot[16];
+    block_reduce_store<14>(v, tot);
     __syncthreads();
     if (threadIdx.x == 0) {
         const bool valid = cc[CC_VALID] != 0.0;
+        const bool llonly = cc[CC_LLONLY] != 0.0;
         bool finite = true;
         for (int q = 0; q < 7; ++q) {
             const double r = valid ? tot[q] + fix7[q] : CUDART_NAN;
-            finite = finite && isfinite(r);
+            if (q == 0 || !llonly) finite = finite && isfinite(r);
             out[q] = r;
+            const double g = fabs(r), bound = tot[7 + q];
+            cc[CC_FTHR + q] = (valid && (q == 0 || !llonly) && bound > FLUSH_TAU * g)
+                                  ? FLUSH_TAU * g / static_cast<double>(nrows > 0 ? nrows : 1)
+                                  : -1.0;
         }
         if (valid && !finite) set_error(ctr, HAWKES_ERR_NONFINITE);
+    }
+}
+
+// Recompute in FP64 the rows that k_reduce's thresholds select (a row whose
+// flush bound for some output exceeds that output's threshold; rows already
+// recomputed for their low rate are left out), replace their FP32 values by
+// the FP64 ones in the outputs, and write their per-row values.  Each block
+// takes 256-row chunks; the last block to finish adds the corrections to out.
+// Returns at once when no output needs it (the usual case).
+__global__ void k_flushfix(const double* __restrict__ acc, const double* __restrict__ t,
+                           const double* __restrict__ x, const double* __restrict__ y,
+                           const double* __restrict__ s, const int32_t* __restrict__ lo,
+                           const int32_t* __restrict__ hi, const double* __restrict__ cc,
+                           int model, int64_t n, int64_t npad, int64_t rb, int64_t re, int* ctr,
+                           double* fix7, double* out, double* rows9) {
+    if (cc[CC_VALID] == 0.0) return;
+    double thr[7];
+    bool any = false;
+    for (int q = 0; q < 7; ++q) {
+        thr[q] = cc[CC_FTHR + q];
+        any = any || thr[q] >= 0.0;
+    }
+    if (!any) return;  // uniform over the grid
+    const bool model1 = (model & HAWKES_MODEL1) != 0;
+    const double tx = cc[CC_TX], tt = cc[CC_TT], om = cc[CC_OM], h = cc[CC_H];
+    const double ix2 = cc[CC_BGT] != 0.0 ? 0.0 : 1.0 / (2.0 * tx * tx);
+    const double it2 = 1.0 / (2.0 * tt * tt), ih2 = 1.0 / (2.0 * h * h);
+    const double flagthr = cc[CC_FLAGTHR];
+    const double mu = cc[CC_MU], th = cc[CC_TH], cB = cc[CC_CB], cE = cc[CC_CE];
+    const double t1 = t[0];
+    __shared__ int list[256];
+    __shared__ int cnt;
+    __shared__ double sums[8];
+    __shared__ int last;
+    double mine[7] = {0, 0, 0, 0, 0, 0, 0};  // thread 0: this block's corrections
+    for (int64_t base = rb + static_cast<int64_t>(blockIdx.x) * 256; base < re;
+         base += static_cast<int64_t>(gridDim.x) * 256) {
+        if (threadIdx.x == 0) cnt = 0;
+        __syncthreads();
+        const int64_t i = base + threadIdx.x;
+        if (threadIdx.x < 256 && i < re) {
+            double sm[6];
+            for (int q = 0; q < 6; ++q) sm[q] = acc[q * npad + i];
+            if (!(mu * cB * sm[0] + th * cE * sm[3] < flagthr)) {
+                double bd[7];
+                const int64_t l = lo[i];
+                row_flush_bound(sm, t[i], t1, l + (n - hi[i]), l, cc, bd);
+                bool f = false;
+                for (int q = 0; q < 7; ++q) f = f || (thr[q] >= 0.0 && bd[q] > thr[q]);
+                if (f) list[atomicAdd(&cnt, 1)] = threadIdx.x;
+            }
+        }
+        __syncthreads();
+        const int m = cnt;
+        for (int k = 0; k < m; ++k) {
+            const int64_t r = base + list[k];
+            double v[6];
+            row_sums64(r, t, x, y, s, lo, hi, model1, n, ix2, it2, ih2, om, v);
+            block_reduce_store<6>(v, sums);
+            if (threadIdx.x == 0) {
+                double s32[6], o64[9], o32[9];
+                for (int q = 0; q < 6; ++q) s32[q] = acc[q * npad + r];
+                row_terms(sums, t[r], cc, o64);
+                row_terms(s32, t[r], cc, o32);
+                for (int q = 0; q < 7; ++q) mine[q] += o64[q] - o32[q];
+                if (rows9)
+                    for (int q = 0; q < 9; ++q) rows9[9 * r + q] = o64[q];
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 7; ++q)
+            if (mine[q] != 0.0) atomicAdd(fix7 + 8 + q, mine[q]);
+        __threadfence();
+        last = atomicAdd(ctr + CT_DONE, 1) == static_cast<int>(gridDim.x) - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile double* fb = fix7 + 8;
+        const bool llonly = cc[CC_LLONLY] != 0.0;
+        bool finite = true;
+        for (int q = 0; q < 7; ++q) {
+            const double r = out[q] + fb[q];
+            out[q] = r;
+            if (q == 0 || !llonly) finite = finite && isfinite(r);
+        }
+        if (!finite) set_error(ctr, HAWKES_ERR_NONFINITE);
     }
 }
 

@@ -27,16 +27,21 @@ namespace hk {
 __global__ void k_prep(const double*, const double*, const double*, const double*, const double*,
                        const hawkes_params*, int, int, int, int64_t, int64_t, Rec*, double*, double*,
                        int*, double*);
-__global__ void k_finalize(const double*, const double*, const double*, int64_t, int64_t, int64_t,
-                           int, int*, int*, double*, double*);
+__global__ void k_finalize(const double*, const double*, const int32_t*, const int32_t*,
+                           const double*, int64_t, int64_t, int64_t, int64_t, int, int*, int*,
+                           double*, double*);
+__global__ void k_flushfix(const double*, const double*, const double*, const double*,
+                           const double*, const int32_t*, const int32_t*, const double*, int,
+                           int64_t, int64_t, int64_t, int64_t, int*, double*, double*, double*);
 __global__ void k_rows64(const double*, const double*, const double*, const double*,
                          const int32_t*, const int32_t*, const double*, int, int64_t, int64_t,
                          int64_t, int64_t, int, const int*, int*, double*, double*, double*);
-__global__ void k_reduce(const double*, int, const double*, const double*, double*, int*);
+__global__ void k_reduce(const double*, int, const double*, double*, int64_t, double*, int*);
 cudaError_t sweep_setup_attributes();
 int sweep_blocks_per_sm(int v);
 int sweep_variant_rows(int v);
-cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt);
+cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt,
+                         bool ll);
 }  // namespace hk
 
 using namespace hk;
@@ -63,8 +68,8 @@ constexpr size_t OFF_REC = OFF_TB + align256((kMaxN / TB) * sizeof(double));
 constexpr size_t OFF_ACC = OFF_REC + align256(kMaxN * sizeof(Rec));
 constexpr size_t OFF_FIX = OFF_ACC + align256(6 * kMaxN * sizeof(double));
 constexpr size_t OFF_PART = OFF_FIX + align256(kMaxN * sizeof(int));
-constexpr size_t OFF_FIX7 = OFF_PART + align256(8 * kMaxFinalBlocks * sizeof(double));
-constexpr size_t OFF_CTR = OFF_FIX7 + align256(8 * sizeof(double));
+constexpr size_t OFF_FIX7 = OFF_PART + align256(PART_STRIDE * kMaxFinalBlocks * sizeof(double));
+constexpr size_t OFF_CTR = OFF_FIX7 + align256(FIX_DOUBLES * sizeof(double));
 constexpr size_t OFF_CC = OFF_CTR + align256(CT_COUNT * sizeof(int));
 constexpr size_t OFF_ITEMS = OFF_CC + align256(CC_COUNT * sizeof(double));
 constexpr size_t SCRATCH_BYTES = OFF_ITEMS + align256(kMaxItems * sizeof(int4));
@@ -96,6 +101,9 @@ __global__ void k_na_setup(const double* __restrict__ t_in, const double* __rest
             const double se = s_in ? s_in[e] : 1.0;
             if (!(se > 0.0) || !isfinite(se) || !isfinite(x_in[e]) || !isfinite(y_in[e]))
                 set_error(ctr, HAWKES_ERR_ARG);
+            // largest -2 log2 s_j above 0 (the excitation flush bound reads it)
+            const float ce = static_cast<float>(-2.0 * log2(se));
+            if (ce > 0.f) atomicMax(ctr + CT_CEMAX, __float_as_int(ce));
             t[e] = te;
             x[e] = x_in[e];
             y[e] = y_in[e];
@@ -248,12 +256,14 @@ extern "C" int hawkes_loglik_grad_noalloc(const double* d_t, const double* d_x, 
     k_na_items<<<1, 32, 0, st>>>(n, tr, c.items);
     k_prep<<<grid, 256, 0, st>>>(c.t, c.x, c.y, c.s, c.tb, d_params, model, 1, 0, n, npad, c.rec,
                                  c.acc, c.cc, c.ctr, c.fix7);
-    if (launch_sweep(&c, true, 0, n, (flags & HAWKES_BG_TIME) != 0) != cudaSuccess) return HAWKES_ERR_CUDA;
-    k_finalize<<<c.final_blocks, 256, 0, st>>>(c.acc, c.t, c.cc, npad, 0, n, 1, c.fixlist, c.ctr,
-                                               c.partials, nullptr);
+    if (launch_sweep(&c, true, 0, n, (flags & HAWKES_BG_TIME) != 0, false) != cudaSuccess) return HAWKES_ERR_CUDA;
+    k_finalize<<<c.final_blocks, 256, 0, st>>>(c.acc, c.t, c.lo, c.hi, c.cc, n, npad, 0, n, 1,
+                                               c.fixlist, c.ctr, c.partials, nullptr);
     k_rows64<<<c.sms, 256, 0, st>>>(c.t, c.x, c.y, c.s, c.lo, c.hi, c.cc, model, n, npad, 0, 0, 1,
                                     c.fixlist, c.ctr, c.acc, c.fix7, nullptr);
-    k_reduce<<<1, 256, 0, st>>>(c.partials, c.final_blocks, c.fix7, c.cc, d_out, c.ctr);
+    k_reduce<<<1, 256, 0, st>>>(c.partials, c.final_blocks, c.fix7, c.cc, n, d_out, c.ctr);
+    k_flushfix<<<c.sms, 256, 0, st>>>(c.acc, c.t, c.x, c.y, c.s, c.lo, c.hi, c.cc, model, n, npad,
+                                      0, n, c.ctr, c.fix7, d_out, nullptr);
     k_na_nan_on_error<<<1, 32, 0, st>>>(c.ctr, d_out);
     return cudaGetLastError() == cudaSuccess ? HAWKES_OK : HAWKES_ERR_CUDA;
 }

@@ -1,6 +1,7 @@
 // Host side of the FP32 pair sweep (kernels in sweep_kernel.cuh): kernel
 // variants, their work lists, and launch.  This unit instantiates the
-// space-time background's kernels; sweep_bgt.cu the time-only background's.
+// space-time background's kernels; sweep_bgt.cu the time-only background's
+// and sweep_ll.cu the log-likelihood-only ones.
 #include <algorithm>
 #include <vector>
 
@@ -8,19 +9,23 @@
 
 namespace hk {
 
-static const Variant kVariants[] = HK_SWEEP_VARIANTS(false);
+static const Variant kVariants[] = HK_SWEEP_VARIANTS(false, false);
 static_assert(sizeof(kVariants) / sizeof(kVariants[0]) == kNumVariants, "variant count");
 
-static const Variant& variant_of(int v, bool bgt) {
-    return bgt ? sweep_variants_bgt()[v] : kVariants[v];
+// The kernel family of a call: the time-only background keeps its own kernels
+// (with the log-likelihood-only flag it forms every moment and the gradient is
+// dropped at finalisation).
+static const Variant& variant_of(int v, bool bgt, bool ll) {
+    return bgt ? sweep_variants_bgt()[v] : ll ? sweep_variants_ll()[v] : kVariants[v];
 }
 
 int sweep_num_variants() { return kNumVariants; }
 int sweep_variant_rows(int v) { return kVariants[v].tr; }
 
 cudaError_t sweep_setup_attributes() {
-    for (int k = 0; k < 2 * kNumVariants; ++k) {
-        const Variant& v = variant_of(k % kNumVariants, k >= kNumVariants);
+    for (int k = 0; k < 3 * kNumVariants; ++k) {
+        const int fam = k / kNumVariants;
+        const Variant& v = variant_of(k % kNumVariants, fam == 1, fam == 2);
         for (SweepFn f : {v.win, v.sym, v.batch}) {
             cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  static_cast<int>(v.smem));
@@ -76,16 +81,25 @@ static ProbDesc desc_of(const hawkes_ctx* c) {
     return ProbDesc{c->t, c->rec, c->lo, c->hi, c->tb, c->cc, c->acc, c->n, c->npad};
 }
 
-cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt) {
-    const Variant& v = variant_of(c->variant, bgt);
+// Symmetric sweep of one problem over the work list items[0, nitems) (the
+// whole list, or one shard's part of it).
+cudaError_t launch_sweep_list(hawkes_ctx* c, const int4* items, int nitems, bool bgt, bool ll) {
+    const Variant& v = variant_of(c->variant, bgt, ll);
+    const int grid_cap = c->sms * c->variant_bpsm;
+    const int grid = nitems < grid_cap ? nitems : grid_cap;
+    if (grid <= 0) return cudaSuccess;
+    v.sym<<<grid, THREADS, v.smem, c->stream>>>(desc_of(c), nullptr, items, nitems, c->ctr, 0,
+                                                c->n, 0, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row_end, bool bgt,
+                         bool ll) {
+    const Variant& v = variant_of(c->variant, bgt, ll);
     const int grid_cap = c->sms * c->variant_bpsm;
     const ProbDesc one = desc_of(c);
     if (sym) {
-        const int nitems = c->nitems;
-        const int grid = nitems < grid_cap ? nitems : grid_cap;
-        if (grid <= 0) return cudaSuccess;
-        v.sym<<<grid, THREADS, v.smem, c->stream>>>(one, nullptr, c->items, nitems, c->ctr,
-                                                    row_begin, row_end, 0, 0);
+        return launch_sweep_list(c, c->items, c->nitems, bgt, ll);
     } else {
         const int item0 = static_cast<int>(row_begin / v.tr);
         const int nrt = static_cast<int>((row_end + v.tr - 1) / v.tr) - item0;
@@ -103,8 +117,9 @@ cudaError_t launch_sweep(hawkes_ctx* c, bool sym, int64_t row_begin, int64_t row
 // One persistent launch over the items of many problems; ctr[CT_WORK] must be
 // zero when it starts.
 cudaError_t launch_sweep_batch(cudaStream_t st, int variant, int grid, const ProbDesc* probs,
-                               int nprobs, const int4* items, int nitems, int* ctr, bool bgt) {
-    const Variant& v = variant_of(variant, bgt);
+                               int nprobs, const int4* items, int nitems, int* ctr, bool bgt,
+                               bool ll) {
+    const Variant& v = variant_of(variant, bgt, ll);
     if (grid > nitems) grid = nitems;
     if (grid <= 0) return cudaSuccess;
     ProbDesc none{};

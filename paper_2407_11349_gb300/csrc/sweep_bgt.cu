@@ -5,7 +5,7 @@
 
 namespace hk {
 
-static const Variant kVariantsBgt[] = HK_SWEEP_VARIANTS(true);
+static const Variant kVariantsBgt[] = HK_SWEEP_VARIANTS(true, false);
 static_assert(sizeof(kVariantsBgt) / sizeof(kVariantsBgt[0]) == kNumVariants, "variant count");
 
 const Variant* sweep_variants_bgt() { return kVariantsBgt; }

@@ -31,6 +31,10 @@
 // and the SBr moment; the excitation is unchanged.  The flag is a template
 // parameter, so the default kernels are compiled exactly as without it.
 //
+// Log-likelihood only (flag HAWKES_LOGLIK_ONLY, template parameter LL): the
+// rows keep SB and SE, the columns SB, and the other moments are not formed
+// (13 algorithmic FP32 operations per unordered pair instead of 19).
+//
 // Work is split into items (row tile x chunk of column tiles) taken from an
 // atomic queue, longest first.  Pair terms are FP32 with exp2 on the SFU;
 // row sums are FP32 within an item (CHUNK x TC sources) and FP64 across
@@ -60,6 +64,7 @@ struct Rows {
 //   EXC    evaluate the excitation term (sources strictly earlier)
 //   COL    also accumulate the background into the source columns
 //   BGT    time-only background (eq. 2): B' = exp(-dt^2/2tau_t^2), no SBr
+//   LL     log-likelihood only: SB and SE (and the column SB) alone
 // rlo/rhi: shared-memory lo/hi of the lane's rows (masked tiles only).
 // racc: the thread's FP32 row accumulators in shared memory (see fold_rows;
 // time-only background only).
@@ -94,7 +99,7 @@ __device__ __forceinline__ void fold_rows(Rows<RP>& rr, float4* __restrict__ rac
     }
 }
 
-template <int RP, int UNROLL, int MASK, bool EXC, bool COL, bool BGT>
+template <int RP, int UNROLL, int MASK, bool EXC, bool COL, bool BGT, bool LL>
 __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j0, int lane,
                                           Rows<RP>& rr, float2 nomt,
                                           const int* __restrict__ rlo,
@@ -136,16 +141,18 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
                     }
                 }
                 rr.sB[p] = add2(rr.sB[p], B);
-                if (!BGT) rr.sBr[p] = fma2(B, r2, rr.sBr[p]);
-                rr.sBt[p] = fma2(B, dt2, rr.sBt[p]);
+                if (!BGT && !LL) rr.sBr[p] = fma2(B, r2, rr.sBr[p]);
+                if (!LL) rr.sBt[p] = fma2(B, dt2, rr.sBt[p]);
                 if (COL && !BGT) {
                     cB = add2(cB, B);
-                    cBr = fma2(B, r2, cBr);
-                    cBt = fma2(B, dt2, cBt);
+                    if (!LL) {
+                        cBr = fma2(B, r2, cBr);
+                        cBt = fma2(B, dt2, cBt);
+                    }
                 }
                 if (COL && BGT) {  // per-step partial (no SBr moment here)
                     pB = (p == 0) ? B : add2(pB, B);
-                    pBt = (p == 0) ? mul2(B, dt2) : fma2(B, dt2, pBt);
+                    if (!LL) pBt = (p == 0) ? mul2(B, dt2) : fma2(B, dt2, pBt);
                 }
                 if (EXC) {
                     const float2 nv = mul2(NB, r2);                  // -beta r~^2
@@ -156,30 +163,34 @@ __device__ __forceinline__ void tile_pass(const float4* __restrict__ tile, int j
                         E.y = (j < rlo[2 * p + 1]) ? E.y : 0.f;
                     }
                     rr.sE[p] = add2(rr.sE[p], E);
-                    rr.sEt[p] = fma2(E, dt, rr.sEt[p]);
-                    rr.sEq[p] = fma2(E, nv, rr.sEq[p]);  // accumulates -sum E beta r~^2
+                    if (!LL) {
+                        rr.sEt[p] = fma2(E, dt, rr.sEt[p]);
+                        rr.sEq[p] = fma2(E, nv, rr.sEq[p]);  // accumulates -sum E beta r~^2
+                    }
                 }
             }
             if (COL) {
                 if (BGT) {
                     cB = add2(cB, pB);
-                    cBt = add2(cBt, pBt);
+                    if (!LL) cBt = add2(cBt, pBt);
                 }
                 const int src = (lane + 1) & 31;
                 cB.x = __shfl_sync(0xffffffffu, cB.x, src);
                 cB.y = __shfl_sync(0xffffffffu, cB.y, src);
-                if (!BGT) {
+                if (!BGT && !LL) {
                     cBr.x = __shfl_sync(0xffffffffu, cBr.x, src);
                     cBr.y = __shfl_sync(0xffffffffu, cBr.y, src);
                 }
-                cBt.x = __shfl_sync(0xffffffffu, cBt.x, src);
-                cBt.y = __shfl_sync(0xffffffffu, cBt.y, src);
+                if (!LL) {
+                    cBt.x = __shfl_sync(0xffffffffu, cBt.x, src);
+                    cBt.y = __shfl_sync(0xffffffffu, cBt.y, src);
+                }
             }
         }
         if (COL) {  // lane k now holds column ch*32 + k, summed over the warp's rows
             atomicAdd(colacc + 0 * TC + ch * 32 + lane, cB.x + cB.y);
-            if (!BGT) atomicAdd(colacc + 1 * TC + ch * 32 + lane, cBr.x + cBr.y);
-            atomicAdd(colacc + 2 * TC + ch * 32 + lane, cBt.x + cBt.y);
+            if (!BGT && !LL) atomicAdd(colacc + 1 * TC + ch * 32 + lane, cBr.x + cBr.y);
+            if (!LL) atomicAdd(colacc + 2 * TC + ch * 32 + lane, cBt.x + cBt.y);
         }
         if (BGT) fold_rows<RP>(rr, racc);
     }
@@ -209,7 +220,7 @@ enum { MODE_WIN = 0, MODE_SYM = 1, MODE_BATCH = 2 };
 //   MODE_WIN:   item k -> row tile item0 + k / nch, column chunk k % nch of
 //               problem `one`, rows [row_begin, row_end) only
 // In MODE_BATCH, nch is the number of problems (checked in debug builds).
-template <int RP, int MINB, int UNROLL, int MODE, bool BGT>
+template <int RP, int MINB, int UNROLL, int MODE, bool BGT, bool LL>
 __global__ void __launch_bounds__(THREADS, MINB)
     k_sweep(ProbDesc one, const ProbDesc* __restrict__ probs, const int4* __restrict__ items,
             int nitems, int* __restrict__ ctr, int64_t row_begin, int64_t row_end, int item0,
@@ -383,17 +394,17 @@ __global__ void __launch_bounds__(THREADS, MINB)
                 if (SYM) {
                     if (j0 < r0 + G::WROWS) {
                         if (j0 + TC > lo_first)
-                            tile_pass<RP, UNROLL, M_LOWER, true, true, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
+                            tile_pass<RP, UNROLL, M_LOWER, true, true, BGT, LL>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                         else
-                            tile_pass<RP, UNROLL, M_NONE, true, true, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
+                            tile_pass<RP, UNROLL, M_NONE, true, true, BGT, LL>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                     }
                 } else {
                     if (j0 + TC <= lo_first)
-                        tile_pass<RP, UNROLL, M_NONE, true, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
+                        tile_pass<RP, UNROLL, M_NONE, true, false, BGT, LL>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                     else if (j0 >= hi_last)
-                        tile_pass<RP, UNROLL, M_NONE, false, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
+                        tile_pass<RP, UNROLL, M_NONE, false, false, BGT, LL>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                     else
-                        tile_pass<RP, UNROLL, M_TWO, true, false, BGT>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
+                        tile_pass<RP, UNROLL, M_TWO, true, false, BGT, LL>(tile, j0, lane, rr, nomt, mylo, myhi, ca, racc);
                 }
             }
             __syncthreads();
@@ -411,8 +422,10 @@ __global__ void __launch_bounds__(THREADS, MINB)
                     double* acc = HK_PD(acc);
                     const int64_t npad = HK_PD(npad);
                     atomicAdd(acc + 0 * npad + j, static_cast<double>(v0));
-                    atomicAdd(acc + 1 * npad + j, static_cast<double>(v1) * cc[CC_SR]);
-                    atomicAdd(acc + 2 * npad + j, static_cast<double>(v2) * cc[CC_ST]);
+                    if (!LL) {
+                        atomicAdd(acc + 1 * npad + j, static_cast<double>(v1) * cc[CC_SR]);
+                        atomicAdd(acc + 2 * npad + j, static_cast<double>(v2) * cc[CC_ST]);
+                    }
                     ca[tid] = 0.f;
                     ca[TC + tid] = 0.f;
                     ca[2 * TC + tid] = 0.f;
@@ -447,6 +460,11 @@ __global__ void __launch_bounds__(THREADS, MINB)
                         vEt = h ? rr.sEt[p].y : rr.sEt[p].x;
                         vEq = h ? rr.sEq[p].y : rr.sEq[p].x;
                     }
+                    if (LL) {
+                        if (vB != 0.f) atomicAdd(acc + 0 * npad + i, static_cast<double>(vB));
+                        if (vE != 0.f) atomicAdd(acc + 3 * npad + i, static_cast<double>(vE));
+                        continue;
+                    }
                     if (vB != 0.f || vBr != 0.f || vBt != 0.f) {
                         atomicAdd(acc + 0 * npad + i, static_cast<double>(vB));
                         atomicAdd(acc + 1 * npad + i, static_cast<double>(vBr) * sr);
@@ -472,9 +490,9 @@ __global__ void __launch_bounds__(THREADS, MINB)
 }
 
 // ---------------------------------------------------------------------------
-// Kernel tables.  Each translation unit that expands HK_SWEEP_VARIANTS(BGT)
-// instantiates one background form's kernels, so the two forms compile in
-// parallel.
+// Kernel tables.  Each translation unit that expands HK_SWEEP_VARIANTS(BGT, LL)
+// instantiates one kernel family (space-time background, time-only
+// background, log-likelihood only), so the families compile in parallel.
 // ---------------------------------------------------------------------------
 using SweepFn = void (*)(ProbDesc, const ProbDesc*, const int4*, int, int*, int64_t, int64_t, int,
                          int);
@@ -486,16 +504,18 @@ struct Variant {
     int tr;
 };
 
-#define HK_VARIANT(RP, MINB, U, BGT)                                                          \
-    {RP, MINB, k_sweep<RP, MINB, U, MODE_WIN, BGT>, k_sweep<RP, MINB, U, MODE_SYM, BGT>,      \
-     k_sweep<RP, MINB, U, MODE_BATCH, BGT>, Geo<RP>::smem(BGT), Geo<RP>::TR}
+#define HK_VARIANT(RP, MINB, U, BGT, LL)                                                      \
+    {RP, MINB, k_sweep<RP, MINB, U, MODE_WIN, BGT, LL>, k_sweep<RP, MINB, U, MODE_SYM, BGT, LL>, \
+     k_sweep<RP, MINB, U, MODE_BATCH, BGT, LL>, Geo<RP>::smem(BGT), Geo<RP>::TR}
 // (rows-per-lane pairs, resident CTAs per SM, unroll of the 32-step pair loop)
-#define HK_SWEEP_VARIANTS(BGT)                                                               \
-    {HK_VARIANT(4, 1, 8, BGT), HK_VARIANT(4, 1, 16, BGT), HK_VARIANT(4, 1, 32, BGT),          \
-     HK_VARIANT(4, 1, 4, BGT), HK_VARIANT(2, 2, 8, BGT)}
+#define HK_SWEEP_VARIANTS(BGT, LL)                                                           \
+    {HK_VARIANT(4, 1, 8, BGT, LL), HK_VARIANT(4, 1, 16, BGT, LL), HK_VARIANT(4, 1, 32, BGT, LL), \
+     HK_VARIANT(4, 1, 4, BGT, LL), HK_VARIANT(2, 2, 8, BGT, LL)}
 constexpr int kNumVariants = 5;
 
-// The time-only background's table (same order as the default one).
+// The time-only background's table and the log-likelihood-only table (same
+// order as the default one).
 const Variant* sweep_variants_bgt();
+const Variant* sweep_variants_ll();
 
 }  // namespace hk

@@ -28,6 +28,7 @@ HAWKES_MODEL1 = 2
 HAWKES_SKIP_UNDERFLOW = 4
 HAWKES_BG_TIME = 8
 HAWKES_SKIP_SPATIAL = 16
+HAWKES_LOGLIK_ONLY = 32
 KERNEL_CLASSES = ("prep", "sweep", "rows64", "final", "reduce", "resample", "other")
 
 
@@ -82,6 +83,11 @@ _SIGS = {
                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D]),
     "hawkes_tune_cache_put": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_double]),
+    "hawkes_shard_bounds": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int64)]),
+    "hawkes_shard_tile_rows": (ctypes.c_int64, [_VP]),
+    "hawkes_shard_moments": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, _VP]),
+    "hawkes_finalize_moments": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, _VP, _VP]),
     "hawkes_loglik_grad_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, _VP,
                                                   ctypes.c_uint32, _VP, _VP]),
     "hawkes_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int32,
@@ -289,6 +295,30 @@ def hawkes_debug_set_item(ctx, k, row_tile, col_begin, col_end):
     """Debug build only: overwrite work item k (a test hook for the checks)."""
     _check(lib().hawkes_debug_set_item(ctx, int(k), int(row_tile), int(col_begin), int(col_end)),
            "hawkes_debug_set_item")
+
+
+def hawkes_shard_bounds(n, tile_rows, nshards):
+    """Row boundaries [nshards + 1] of the symmetric sweep's split into shards
+    of about equal pair counts (host only; no device needed)."""
+    b = (ctypes.c_int64 * (int(nshards) + 1))()
+    _check(lib().hawkes_shard_bounds(int(n), int(tile_rows), int(nshards), b), "hawkes_shard_bounds")
+    return np.array(list(b), dtype=np.int64)
+
+
+def hawkes_shard_tile_rows(ctx):
+    r = int(lib().hawkes_shard_tile_rows(ctx))
+    _check(min(r, 0), "hawkes_shard_tile_rows")
+    return r
+
+
+def hawkes_shard_moments(ctx, d_params, flags, shard, nshards, d_moments):
+    _check(lib().hawkes_shard_moments(ctx, _VP(int(d_params)), int(flags), int(shard), int(nshards),
+                                      _VP(int(d_moments))), "hawkes_shard_moments")
+
+
+def hawkes_finalize_moments(ctx, d_params, flags, d_moments, d_out):
+    _check(lib().hawkes_finalize_moments(ctx, _VP(int(d_params)), int(flags), _VP(int(d_moments)),
+                                         _VP(int(d_out))), "hawkes_finalize_moments")
 
 
 HAWKES_NOALLOC_MAX_N = 65536
@@ -535,6 +565,20 @@ class Hawkes:
 
     def set_variant(self, v):
         hawkes_set_sweep_variant(self.ctx, v)
+
+    def tile_rows(self):
+        """Rows per row tile of the current sweep variant (the shard granularity)."""
+        return hawkes_shard_tile_rows(self.ctx)
+
+    def shard_moments(self, d_params, shard, nshards, d_moments, flags=HAWKES_F32):
+        """Queue shard `shard` of `nshards` of the symmetric sweep; its six
+        moment vectors (6 x n doubles) go to device memory d_moments."""
+        hawkes_shard_moments(self.ctx, d_params, flags, shard, nshards, d_moments)
+
+    def finalize_moments(self, d_params, d_moments, d_out, flags=HAWKES_F32):
+        """Queue the finalisation of moment vectors summed over all shards:
+        ell and the six partials to device memory d_out[7]."""
+        hawkes_finalize_moments(self.ctx, d_params, flags, d_moments, d_out)
 
     @property
     def variant(self):

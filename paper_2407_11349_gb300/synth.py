@@ -24,6 +24,8 @@ source bandwidth scale of the spatially varying model (eq. 3).
 """
 from dataclasses import dataclass, field
 
+import math
+
 import numpy as np
 
 # Parameter vector used by every workload: mu, tau_x (km), tau_t (d), theta,
@@ -62,8 +64,10 @@ class Counties:
         return out
 
     def scale(self):
-        """s_c = (density_c / median)^(-1/2)."""
-        return (self.density / np.median(self.density)) ** -0.5
+        """s_c = (density_c / median)^(-1/2), through a correctly rounded
+        square root and division, so that the values are the same on every
+        platform (a power function is not correctly rounded)."""
+        return 1.0 / np.sqrt(self.density / np.median(self.density))
 
 
 @dataclass
@@ -151,7 +155,9 @@ def voronoi_counties(n_cells, width, height, rng, log_sd=1.3):
         if len(keep) > 1 and np.hypot(*(poly[keep[-1]] - poly[0])) <= 1e-9:
             keep.pop()
         polys.append(poly[keep])
-    dens = np.exp(rng.normal(0.0, log_sd, size=n_cells))
+    # exp of each draw through the C library, element by element: vectorised
+    # exp implementations differ in the last bit between platforms
+    dens = np.array([math.exp(v) for v in rng.normal(0.0, log_sd, size=n_cells)])
     return Counties(polys, dens)
 
 
@@ -347,3 +353,41 @@ def config_dataset(which, seed=None):
     if which == "c4":
         return voronoi_dataset(250_000, seed=3 if seed is None else seed, name="c4")
     raise ValueError(which)
+
+
+def fingerprint(arrays):
+    """Identify a workload's input arrays (name -> float64 array).
+
+    ``sha256`` is the exact bytes.  ``stats`` are, per array, its length, the
+    sums of a, a^2 and a * w (w_k = 1 + (k mod 97), fixed weights) and the
+    values at eleven evenly spaced positions: two workloads whose arrays
+    differ only in the last bit of a few elements (a platform's library exp
+    or log) agree on them to about 1e-15 relative, while any other change
+    moves them grossly.  ``same_inputs`` compares two stats records."""
+    import hashlib
+    h = hashlib.sha256()
+    stats = {}
+    for name in sorted(arrays):
+        a = np.ascontiguousarray(arrays[name], dtype=np.float64)
+        h.update(name.encode())
+        h.update(a.tobytes())
+        w = 1.0 + (np.arange(a.size) % 97)
+        pos = np.linspace(0, max(a.size - 1, 0), 11).astype(np.int64)
+        stats[name] = {"n": int(a.size), "sum": float(a.sum()), "sum2": float((a * a).sum()),
+                       "sumw": float((a * w).sum()), "at": [float(a[k]) for k in pos] if a.size else []}
+    return {"sha256": h.hexdigest(), "stats": stats}
+
+
+def same_inputs(a, b, rel=1e-12):
+    """True if two ``fingerprint(...)['stats']`` records describe the same
+    arrays up to last-bit differences."""
+    if sorted(a) != sorted(b):
+        return False
+    for k in a:
+        x, y = a[k], b[k]
+        if x["n"] != y["n"] or len(x["at"]) != len(y["at"]):
+            return False
+        for u, v in [(x["sum"], y["sum"]), (x["sum2"], y["sum2"]), (x["sumw"], y["sumw"])] + list(zip(x["at"], y["at"])):
+            if abs(u - v) > rel * max(abs(u), abs(v), 1e-300):
+                return False
+    return True

@@ -70,3 +70,35 @@ def test_training_fits_a_smooth_function():
         assert np.median(err) < 0.05
     finally:
         net.close()
+
+
+def test_predict_matches_reference_element_by_element():
+    """hawkes_mlp_predict against the reference forward pass after the same
+    standardisation: inputs (q - mean_in) / sd_in with a constant 1 appended,
+    outputs mean_out + sd_out * y, with the network's stored weights and the
+    GPU's BF16 rounding points; every element within 2e-4 of its column's
+    output scale (sd_out)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(17)
+    X = rng.normal(size=(500, 6)) * np.array([0.1, 0.2, 0.3, 0.1, 0.2, 0.4]) + np.log([0.5, 20, 7, 0.3, 0.2, 2])
+    Y = np.column_stack([rng.normal(-1e6, 300.0, 500), rng.normal(0, 50.0, (500, 6))])
+    net = MLP(0, seed=9)
+    try:
+        net.set_data(X, Y)
+        net.train(200, batch=128, lr=1e-3, seed=2)
+        theta = net.get_params().astype(np.float64)
+        st = net.stats()
+        q = X[:77] + rng.normal(0, 0.05, (77, 6))
+        dq = torch.tensor(q, dtype=torch.float64, device="cuda")
+        dout = torch.zeros((77, 7), dtype=torch.float64, device="cuda")
+        net.predict(dq.data_ptr(), 77, dout.data_ptr())
+        net.wait()
+        got = dout.cpu().numpy()
+    finally:
+        net.close()
+    xs = (q - st[:6]) / st[6:12]
+    xin = np.column_stack([xs.astype(np.float32).astype(np.float64), np.ones(77)])
+    y, _ = mo.forward(theta, xin, bf16=True)
+    want = st[12:19] + st[19:26] * y
+    err = np.abs(got - want) / st[19:26]
+    assert np.max(err) <= 2e-4, np.max(err, axis=0)

@@ -424,9 +424,11 @@ def test_spatial_skip_matches_oracle(hk, n, window, ties, model1):
     fl = HAWKES_F32 | HAWKES_SKIP_SPATIAL | (HAWKES_MODEL1 if model1 else 0)
     ll, g = hk.loglik_grad(P0, fl)
     assert_close(ll, g, ref, rows, TOL_LL32, TOL_G32, f"spatial n={n} window={window}")
-    # other bandwidths, same order (wide enough that every component has
-    # terms within FP32 range on these sparse events)
-    p2 = (2.0, 50.0, 10.0, 0.9, 0.05, 20.0)
+    # other bandwidths, same order: on these sparse events (1,200 days) every
+    # excitation term but a few is below FP32's 2^-126, so d/dh and d/domega
+    # rest on terms FP32 flushes; the flush-bound fix-up recomputes the rows
+    # that carry them in FP64
+    p2 = (2.0, 5.0, 2.0, 0.9, 1.5, 0.7)
     ll2, g2 = hk.loglik_grad(p2, fl)
     ref2, rows2 = oracle.loglik_grad(ds.t, ds.x, ds.y, p2, s=s, rows=True)
     assert_close(ll2, g2, ref2, rows2, TOL_LL32, TOL_G32, f"spatial n={n} other parameters")
@@ -467,3 +469,85 @@ def test_spatial_skip_rejects_what_it_does_not_cover(hk):
         hk.set_spatial_window(100)
     ll, g = hk.loglik_grad(P0, HAWKES_F32)  # still usable
     assert np.isfinite(ll)
+
+
+# ---------------------------------------------------------------------------
+# Terms below FP32's range: the flush-bound fix-up of the FP32 path
+# ---------------------------------------------------------------------------
+
+def raw_rel(got, ref):
+    """Relative error of each output against its own magnitude (no floor)."""
+    return np.abs(np.asarray(got) - ref) / np.maximum(np.abs(ref), 1e-300)
+
+
+@pytest.mark.parametrize("n,p", [(300, (2.0, 5.0, 2.0, 0.9, 1.5, 0.7)), (6000, (2.0, 5.0, 2.0, 0.9, 1.5, 0.7)),
+                                 (3000, (0.5, 0.05, 0.01, 0.3, 50.0, 0.01))])
+@pytest.mark.parametrize("extra", [0, HAWKES_SKIP_UNDERFLOW])
+def test_flushed_terms_fp32_path_matches_oracle_unfloored(hk, n, p, extra):
+    """Sparse events (1,200 days, 20 x 20 grid of 50 km counties) at
+    bandwidths where nearly every excitation term, or every term, is below
+    2^-126: the outputs that rest on those terms are tiny but nonzero in the
+    oracle.  The FP32 path must still give every output within 1e-6 (ell)
+    and 1e-5 (each partial) of the oracle relative to the output itself."""
+    ds = synth.grid_dataset(n, 1200.0, 20, 20, seed=70 + n)
+    hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
+    ref, rows = oracle.loglik_grad(ds.t, ds.x, ds.y, p, s=ds.s, rows=True)
+    ll, g = hk.loglik_grad(p, HAWKES_F32 | extra)
+    e = raw_rel(np.concatenate([[ll], g]), ref)
+    assert e[0] <= TOL_LL32 and np.all(e[1:] <= TOL_G32), f"raw rel errs {e} (ref {ref})"
+    out, rws = hk.loglik_rows(p, HAWKES_F32 | extra)  # per-row values follow the fix-up
+    assert np.allclose(out, np.concatenate([[ll], g]), rtol=1e-12, atol=0)
+    assert abs(rws[:, 0].sum() - out[0]) <= 1e-9 * abs(out[0])
+    assert np.all(raw_rel(rws[:, 1:7].sum(axis=0), out[1:]) <= 1e-9)
+
+
+def test_flush_fixup_is_idle_at_normal_bandwidths(hk):
+    """At the workload's parameters no row is recomputed for the flush bound:
+    the outputs equal those of the sweep alone, so the FP32 path costs what
+    it did before the fix-up existed (checked through the per-kernel
+    timing: the fix-up kernel returns at once)."""
+    ds = synth.config_dataset("c2")
+    hk.load(ds)
+    hk.profile(True)
+    hk.loglik_grad(P0, HAWKES_F32)
+    prof = hk.profile(False)
+    launches, ms = prof["rows64"]
+    assert launches == 2 and ms < 0.2, prof  # the floor-rate rows and the idle fix-up
+
+
+# ---------------------------------------------------------------------------
+# Full-size totals at N = 1,000,000 (c3)
+# ---------------------------------------------------------------------------
+
+def _golden_c3():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_c3.json")
+    return json.load(open(path)) if os.path.exists(path) else None
+
+
+def test_c3_totals_against_fp64_path_and_stored_oracle(hk):
+    """The whole N = 1,000,000 sum after resample(2, 0, 0): the FP32 path's
+    seven totals against the FP64 GPU path at full size, and both against the
+    oracle's values stored in tests/golden/oracle_c3.json (written by
+    tests/golden/make_golden_c3.py from the oracle alone) once the inputs are
+    checked to be the same.  Errors are relative to each output itself, with
+    no floor: 1e-6 (ell) and 1e-5 (each partial) for FP32, 1e-10 for FP64."""
+    ds = synth.config_dataset("c3")
+    hk.load(ds)
+    hk.resample(2, 0, 0)
+    x, y = hk.locations()
+    f32 = np.concatenate(hk.loglik_grad(P0, HAWKES_F32), axis=None)
+    f64 = np.concatenate(hk.loglik_grad(P0, HAWKES_F64), axis=None)
+    e = raw_rel(f32, f64)
+    print("c3 FP32 vs FP64 GPU, raw relative errors:", e)
+    assert e[0] <= TOL_LL32 and np.all(e[1:] <= TOL_G32), e
+    doc = _golden_c3()
+    assert doc is not None, "tests/golden/oracle_c3.json missing"
+    fp = synth.fingerprint({"t": ds.t, "x": x, "y": y, "s": ds.s})
+    assert synth.same_inputs(fp["stats"], doc["inputs"]["stats"]), "c3 inputs differ from the stored ones"
+    ref = np.array(doc["loglik_grad"])
+    e32, e64 = raw_rel(f32, ref), raw_rel(f64, ref)
+    print("c3 against the stored oracle: FP32", e32, "FP64", e64)
+    assert np.all(e64 <= TOL_F64), e64
+    assert e32[0] <= TOL_LL32 and np.all(e32[1:] <= TOL_G32), e32

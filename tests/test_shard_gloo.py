@@ -70,6 +70,52 @@ def test_row_bounds_partition():
         assert max(sizes) - min(sizes) <= 1
 
 
+def _symmetric_worker(rank, world, port, out_path):
+    """Each rank evaluates the rows of its symmetric shard (bounds from the
+    library's host-only partition) with the CPU oracle; one all-reduce of 7
+    doubles gives the whole."""
+    import oracle
+    from paper_2407_11349_gb300 import shard
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    ds = _data()
+    b = shard.symmetric_row_bounds(ds.n, 128, world)
+    o = oracle.loglik_grad(ds.t, ds.x, ds.y, ds.params, s=ds.s, row_begin=int(b[rank]),
+                           row_end=int(b[rank + 1]), threads=1)
+    t = torch.tensor(o, dtype=torch.float64)
+    dist.all_reduce(t)
+    if rank == 0:
+        np.save(out_path, t.numpy())
+    dist.destroy_process_group()
+
+
+def test_symmetric_bounds_balance_pairs():
+    """Whole row tiles, covering [0, n) in order, each shard's pairs (i, j < i)
+    within one tile's worth of an equal share."""
+    from paper_2407_11349_gb300 import shard
+    for n, tr, w in ((1_000_000, 2048, 2), (1_000_000, 2048, 4), (1_000_000, 1024, 8), (250_000, 2048, 3),
+                     (5000, 2048, 4), (1, 2048, 2)):
+        b = shard.symmetric_row_bounds(n, tr, w)
+        assert b[0] == 0 and b[-1] == n and np.all(np.diff(b) >= 0)
+        assert np.all(b[1:-1] % tr == 0)
+        pairs = np.array([(e - a) * (a + e - 1) / 2 for a, e in zip(b[:-1], b[1:])])
+        total = n * (n - 1) / 2
+        last_tile = tr * n  # pairs of the largest row tile
+        assert np.all(np.abs(pairs - total / w) <= last_tile), (n, w, pairs)
+        if n >= 8 * tr * w:  # boundaries near n sqrt(g / G)
+            want = n * np.sqrt(np.arange(w + 1) / w)
+            assert np.all(np.abs(b - want) <= tr)
+
+
+def test_two_rank_symmetric_shard_rows_sum_to_whole(tmp_path):
+    import oracle
+    out = str(tmp_path / "sym.npy")
+    mp.spawn(_symmetric_worker, args=(2, _free_port(), out), nprocs=2, join=True)
+    got = np.load(out)
+    ds = _data()
+    ref = oracle.loglik_grad(ds.t, ds.x, ds.y, ds.params, s=ds.s)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+
+
 def test_two_rank_sharded_sum_equals_whole(tmp_path):
     import oracle
     out = str(tmp_path / "sum.npy")

@@ -5,12 +5,17 @@ It exists for callers that cannot allocate device memory (code inside a
 device allocator or memory-pool callback, applications that pre-reserve all
 device memory): it takes the caller's device buffers and works in a fixed
 scratch array built into the library.  Here the test plays such a caller: it
-owns the input and output buffers, calls the entry point twice in a row
-through the C ABI (different sizes and models, so the second call sees the
-first call's leftovers in the shared scratch), and compares each result with
-hawkes_loglik_grad on the same events, within the FP32-path tolerances of
-the parity tests: 1e-6 relative on the log-likelihood, 1e-5 on each gradient
-component relative to max(|g_k|, 1e-3 sum_i |d ell_i / d p_k|).
+owns the input and output buffers, calls the entry point several times in a
+row through the C ABI (different sizes and models, so each call sees the
+previous call's leftovers in the shared scratch, up to the largest size the
+scratch holds), and compares each result with hawkes_loglik_grad on the
+same events and, at the largest size, with the FP64 CPU oracle, within the
+FP32-path tolerances of the parity tests: 1e-6 relative on the
+log-likelihood, 1e-5 on each gradient component relative to
+max(|g_k|, 1e-3 sum_i |d ell_i / d p_k|).  It also checks what the entry
+point is for: a repeated call changes neither PyTorch's allocated bytes nor
+the device's free memory; and that bad input made on the host (unsorted
+times, a negative bandwidth) comes back as seven NaN outputs.
 
 The file name sorts last so that a run stopping at the first failure has run
 every other test before this one.
@@ -44,6 +49,7 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
     cases = [
         (synth.grid_dataset(40_000, 400.0, 40, 40, seed=21), HAWKES_F32),
         (synth.grid_dataset(5_000, 100.0, 20, 20, seed=22), HAWKES_F32 | HAWKES_MODEL1),
+        (synth.grid_dataset(HAWKES_NOALLOC_MAX_N, 600.0, 40, 40, seed=24), HAWKES_F32),
         (synth.grid_dataset(3_000, 100.0, 20, 20, seed=23), HAWKES_F32 | HAWKES_BG_TIME),
     ]
     hk = Hawkes(0)
@@ -69,8 +75,65 @@ def test_noalloc_matches_regular_entry_point_on_two_calls():
             hk.set_events(ds.t, ds.county, ds.county_scale, ds.x, ds.y)
             ref, rows = hk.loglik_rows(P0, flags)
             _close(got, ref, rows)
+            if ds.n == HAWKES_NOALLOC_MAX_N:  # the largest size: also against the oracle
+                import oracle
+                oref, orows = oracle.loglik_grad(ds.t, ds.x, ds.y, P0, s=ds.s, rows=True)
+                _close(got, oref, orows)
     finally:
         hk.close()
+
+
+def test_noalloc_repeated_call_allocates_nothing():
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    ds = synth.grid_dataset(8_000, 100.0, 20, 20, seed=25)
+    t, x, y, s = (torch.tensor(a, dtype=torch.float64, device=dev) for a in (ds.t, ds.x, ds.y, ds.s))
+    p = torch.tensor(P0, dtype=torch.float64, device=dev)
+    out = torch.empty(7, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def call():
+        hawkes_loglik_grad_noalloc(t.data_ptr(), x.data_ptr(), y.data_ptr(), s.data_ptr(), ds.n,
+                                   p.data_ptr(), HAWKES_F32, out.data_ptr(), stream)
+        torch.cuda.synchronize(dev)
+        return out.cpu().numpy().copy()
+
+    first = call()  # may set the device up and load the kernels
+    alloc0, free0 = torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0]
+    second = call()
+    alloc1, free1 = torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0]
+    assert alloc1 == alloc0 and free1 == free0, (alloc0, alloc1, free0, free1)
+    # the same result up to the order of the FP32 atomics
+    assert np.all(np.isfinite(second)) and np.allclose(first, second, rtol=1e-6, atol=0)
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "tau_x"])
+def test_noalloc_bad_input_gives_nan(bad):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    ds = synth.grid_dataset(2_000, 100.0, 20, 20, seed=26)
+    tt = ds.t.copy()
+    pp = np.array(P0, dtype=np.float64)
+    if bad == "unsorted":
+        tt[[10, 11]] = tt[[11, 10]] + np.array([0.0, 1e-3])  # t[10] > t[11]
+        assert tt[10] > tt[11]
+    else:
+        pp[1] = -1.0
+    t, x, y, s = (torch.tensor(a, dtype=torch.float64, device=dev) for a in (tt, ds.x, ds.y, ds.s))
+    p = torch.tensor(pp, dtype=torch.float64, device=dev)
+    out = torch.zeros(7, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    hawkes_loglik_grad_noalloc(t.data_ptr(), x.data_ptr(), y.data_ptr(), s.data_ptr(), ds.n,
+                               p.data_ptr(), HAWKES_F32, out.data_ptr(), stream)
+    torch.cuda.synchronize(dev)
+    assert np.all(np.isnan(out.cpu().numpy()))
+    # the next good call is clean: every call clears the error flag
+    p.copy_(torch.tensor(P0, dtype=torch.float64))
+    t.copy_(torch.tensor(ds.t, dtype=torch.float64))
+    hawkes_loglik_grad_noalloc(t.data_ptr(), x.data_ptr(), y.data_ptr(), s.data_ptr(), ds.n,
+                               p.data_ptr(), HAWKES_F32, out.data_ptr(), stream)
+    torch.cuda.synchronize(dev)
+    assert np.all(np.isfinite(out.cpu().numpy()))
 
 
 def test_noalloc_rejects_sizes_above_its_limit():
