@@ -235,10 +235,15 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     init = np.tile(eta0, (chains, 1)) + np.random.default_rng(4).normal(0, 0.01, (chains, 6))
     ex = hmc.Sampler(tgt, prior, init, n_leapfrog=leapfrog, seed=1, cut=cut)
     ex.record = []
+    # under the cut scheme the warmup also records each location draw's
+    # feature: the exact log-likelihood at a fixed anchor (the starting
+    # point) under that draw, the seventh input of the feature network
+    a_f = eta0.copy() if cut else None
     t0 = time.perf_counter()
-    last = ex.warmup(warmup)
+    last = ex.warmup(warmup, feature_anchor=a_f)
     t_warm = time.perf_counter() - t0
-    X, Y = hmc.training_set(ex.record[1 + last * (leapfrog + 1):])
+    rec = ex.record[1 + last * (leapfrog + 1):]
+    X, Y = hmc.training_set(rec)
     ex.record = None
     net = MLP(torch_device(), seed=2)
     t0 = time.perf_counter()
@@ -247,6 +252,13 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     t_train = time.perf_counter() - t0
     q_start, eps, cov = ex.q.copy(), ex.eps.copy(), ex.cov.copy()
     field = hmc.SurrogateField(net, chains)
+    net_f = field_f = None
+    if cut:
+        Xf, Yf, Ff = hmc.training_set(rec, with_feature=True)
+        net_f = MLP(torch_device(), seed=2)
+        net_f.set_data(Xf, Yf, Ff)
+        loss_f = net_f.train(4000, batch=512, lr=1e-3, seed=3)
+        field_f = hmc.SurrogateField(net_f, chains, feature=True)
 
     def run(sampler, **kw):
         n0 = tgt.n_exact
@@ -266,6 +278,11 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     summaries, res = {}, {}
     summaries["exact"], res["exact"] = run(ex)
     summaries["surrogate"], res["surrogate"] = run(hmc_sampler(5), field=field)
+    if cut:
+        # the network told about each draw through its seventh input
+        summaries["surrogate_feature"], res["surrogate_feature"] = run(hmc_sampler(9), field=field_f,
+                                                                       feature_anchor=a_f)
+        res["surrogate_feature"]["train_loss"] = loss_f
     if not lite:
         # the anchored surrogate: each iteration's field is shifted by the
         # exact minus the network's gradient at a fixed anchor (the median of
@@ -307,6 +324,8 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
                                          for i, k in enumerate(hmc.NAMES)}
                                     for nm, sm in summaries.items() if nm != "univariate_mh"}}
     net.close()
+    if net_f is not None:
+        net_f.close()
     tgt.close()
     out = {"n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
            "draws_per_chain": draws, "training_pairs": int(X.shape[0]), "train_loss": loss,
@@ -322,6 +341,41 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
            "note": "all samplers share the exact-HMC warmup's step size and dense metric; the surrogate "
                    "is trained on the warmup's exact evaluations; data: clustered synthetic events on a "
                    "40x40 grid of 50 km counties over 1,200 days"}
+    return out
+
+
+def bench_mh(n_events, chains=30, warmup=150, draws=400, flags=0, seed=4):
+    """The paper's sampler at its chain count (Sec. 2.2, 3.2): univariate
+    random-walk Metropolis-Hastings on log-parameters under the cut scheme,
+    all chains in lockstep, each update one batched log-likelihood-only
+    evaluation of every chain.  Reports the worst parameter's bulk and tail
+    ESS and R-hat, as the paper's Sec. 3.2 does, and the time."""
+    from paper_2407_11349_gb300 import diagnostics as dg
+    from paper_2407_11349_gb300 import hmc, synth
+    ds = synth.clustered_dataset(n_events, T=1200.0, nx=40, ny=40, seed=seed)
+    eta0 = np.log(synth.DEFAULT_PARAMS)
+    prior = hmc.Prior(eta0)
+    tgt = hmc.HawkesTarget(ds, chains, seed=seed, flags=flags)
+    init = np.tile(eta0, (chains, 1)) + np.random.default_rng(seed).normal(0, 0.01, (chains, 6))
+    mh = hmc.MHSampler(tgt, prior, init, seed=6, cut=True)
+    t0 = time.perf_counter()
+    mh.warmup(warmup)
+    t_warm = time.perf_counter() - t0
+    n0 = tgt.n_exact
+    d, acc, sec = mh.sample(draws)
+    summ = dg.summary(d, hmc.NAMES)
+    worst = min(hmc.NAMES, key=lambda k: summ[k]["bulk_ess"])
+    out = {"n_events": ds.n, "chains": chains, "warmup_iters": warmup, "draws_per_chain": draws,
+           "seconds_warmup": t_warm, "seconds_sampling": sec, "accept": float(acc.mean()),
+           "evaluations": tgt.n_exact - n0, "evaluations_per_s": (tgt.n_exact - n0) / sec,
+           "worst_parameter": worst, "worst_bulk_ess": summ[worst]["bulk_ess"],
+           "worst_tail_ess": min(v["tail_ess"] for v in summ.values()),
+           "max_rhat": max(v["rhat"] for v in summ.values()),
+           "min_bulk_ess_per_s": summ[worst]["bulk_ess"] / sec,
+           "summary": summ,
+           "note": "log-likelihood-only batched evaluations (HAWKES_LOGLIK_ONLY); clustered synthetic "
+                   "events on a 40x40 grid of 50 km counties over 1,200 days"}
+    tgt.close()
     return out
 
 
@@ -444,6 +498,14 @@ def main():
                     help="with --hmc-only: locations held fixed instead of the cut scheme")
     ap.add_argument("--hmc-spatial", action="store_true",
                     help="with --hmc-only: exact evaluations with the spatial skip (chain by chain)")
+    ap.add_argument("--mh-only", action="store_true",
+                    help="run only the paper's univariate MH sampler (30 chains, log-likelihood only)")
+    ap.add_argument("--mh-n", type=int, default=100_000)
+    ap.add_argument("--mh-chains", type=int, default=30)
+    ap.add_argument("--mh-warmup", type=int, default=150)
+    ap.add_argument("--mh-draws", type=int, default=400)
+    ap.add_argument("--hmc-ref-rounds", type=int, default=0,
+                    help="with --hmc-only: location draws per chain of the cut-posterior reference")
     ap.add_argument("--hmc-chains", type=int, default=4)
     ap.add_argument("--hmc-warmup", type=int, default=300)
     ap.add_argument("--hmc-draws", type=int, default=300)
@@ -471,12 +533,18 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.mh_only:
+        torch.cuda.set_stream(torch.cuda.Stream())
+        r = bench_mh(args.mh_n, chains=args.mh_chains, warmup=args.mh_warmup, draws=args.mh_draws,
+                     flags=HAWKES_SKIP_UNDERFLOW)
+        print(json.dumps({"mh_only": r}))
+        return
     if args.hmc_only:
         # one HMC comparison at a chosen size (exact vs surrogate; an exact
         # skip of zero terms on: same results, less work)
         torch.cuda.set_stream(torch.cuda.Stream())
         r = bench_hmc(args.hmc_n, cut=not args.hmc_fixed, chains=args.hmc_chains, warmup=args.hmc_warmup,
-                      draws=args.hmc_draws, lite=True,
+                      draws=args.hmc_draws, lite=True, ref_rounds=args.hmc_ref_rounds,
                       flags=HAWKES_SKIP_SPATIAL if args.hmc_spatial else HAWKES_SKIP_UNDERFLOW)
         print(json.dumps({"hmc_only": r}))
         return
@@ -731,6 +799,8 @@ def main():
                           "fixed_locations": bench_hmc(args.hmc_n, cut=False)}
             out["hmc_cut_surrogate_ess_per_s_ratio"] = out["hmc"]["cut_posterior"]["speedup_ess_per_s"]
             out["hmc_fixed_surrogate_ess_per_s_ratio"] = out["hmc"]["fixed_locations"]["speedup_ess_per_s"]
+            out["hmc_cut_feature_surrogate_ess_per_s_ratio"] = \
+                out["hmc"]["cut_posterior"]["surrogate_feature"]["ess_per_s_vs_exact"]
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(ds)
         print(json.dumps(out))

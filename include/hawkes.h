@@ -428,8 +428,12 @@ int hawkes_batch_tune_cached(hawkes_batch* batch, const hawkes_params* d_params,
 /*
  * Surrogate network (no counterpart in the paper: the learned part layered on
  * its method).  A 7 -> 256 -> 256 -> 7 multilayer perceptron with tanh hidden
- * units maps (six standardised log-parameters, 1) to the standardised
- * log-likelihood and its six log-parameter partials d ell / d log p_k.
+ * units maps (six standardised log-parameters, z) to the standardised
+ * log-likelihood and its six log-parameter partials d ell / d log p_k, where
+ * z is either the constant 1 or a standardised feature supplied with each
+ * sample (e.g. a summary of the location draw the log-likelihood was
+ * evaluated under, so that the network can follow the cut posterior's
+ * draw-to-draw changes).
  * Trained on the GPU by this library's kernels (BF16 products on the
  * 5th-generation tensor cores with the FP32 accumulator in tensor memory for
  * the 256 x 256 layer, FP32 elsewhere, Adam), evaluated inside HMC leapfrog
@@ -451,12 +455,14 @@ int hawkes_mlp_get_params(hawkes_mlp* mlp, float* params);        /* host [NPARA
 int hawkes_mlp_set_params(hawkes_mlp* mlp, const float* params);  /* also resets the Adam state */
 
 /*
- * Training set: X[n x 6] log-parameters and Y[n x 7] (log-likelihood, six
- * log-parameter partials), host arrays, n >= 2.  Column means and standard
- * deviations are computed on the device; inputs and targets are standardised
- * with them (and predictions are mapped back).
+ * Training set: X[n x 6] log-parameters, F[n] the feature of each sample (or
+ * NULL: the seventh input is the constant 1) and Y[n x 7] (log-likelihood,
+ * six log-parameter partials), host arrays, n >= 2.  Column means and
+ * standard deviations are computed on the device; inputs, feature and
+ * targets are standardised with them (and predictions are mapped back).
  */
-int hawkes_mlp_set_data(hawkes_mlp* mlp, int64_t n, const double* X, const double* Y);
+int hawkes_mlp_set_data(hawkes_mlp* mlp, int64_t n, const double* X, const double* F,
+                        const double* Y);
 
 /*
  * `steps` Adam steps (learning rate lr, betas 0.9 / 0.999) on minibatches of
@@ -478,13 +484,20 @@ int hawkes_mlp_loss_grad(hawkes_mlp* mlp, int batch, const float* Xs, const floa
 
 /*
  * Predictions for `count` (1..4096) parameter vectors: d_logp[count x 6]
- * device log-parameters -> d_out[count x 7] device (log-likelihood, six
- * log-parameter partials), queued on the network's stream.
+ * device log-parameters and d_feature[count] their features (device; NULL
+ * exactly when the training set had none, else HAWKES_ERR_STATE) ->
+ * d_out[count x 7] device (log-likelihood, six log-parameter partials),
+ * queued on the network's stream.
  */
-int hawkes_mlp_predict(hawkes_mlp* mlp, int64_t count, const double* d_logp, double* d_out);
+int hawkes_mlp_predict(hawkes_mlp* mlp, int64_t count, const double* d_logp,
+                       const double* d_feature, double* d_out);
 
-/* Standardisation statistics: mean_in[6], sd_in[6], mean_out[7], sd_out[7] (host, 26 doubles). */
-int hawkes_mlp_stats(hawkes_mlp* mlp, double* stats26);
+/*
+ * Standardisation statistics (host, 28 doubles): mean_in[6], sd_in[6],
+ * mean_out[7], sd_out[7], then the feature's mean and sd (0 and 1 without a
+ * feature).
+ */
+int hawkes_mlp_stats(hawkes_mlp* mlp, double* stats28);
 
 /* Wait for the network's queued work. */
 int hawkes_mlp_wait(hawkes_mlp* mlp);

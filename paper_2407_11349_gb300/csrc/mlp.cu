@@ -3,8 +3,9 @@
 // these kernels and evaluated inside HMC leapfrog trajectories.  The paper has
 // no surrogate: this is the learned part layered on its method.
 //
-// Inputs are the six standardised log-parameters and a constant 1; outputs
-// are the standardised log-likelihood and its six log-parameter partials.
+// Inputs are the six standardised log-parameters and a seventh input that is
+// either a constant 1 or a standardised per-sample feature; outputs are the
+// standardised log-likelihood and its six log-parameter partials.
 // Weights are kept in FP32 (Adam state and master copy); the 256 x 256 layer
 // runs on the 5th-generation tensor cores (tcgen05.mma, accumulator in tensor
 // memory) from BF16 copies of W2 and W2^T with BF16 activations and FP32
@@ -368,13 +369,22 @@ __global__ void k_step_done(int64_t* step) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *step += 1;
 }
 
-// Column means and standard deviations (FP64) of X[n x 6] and Y[n x 7], then
-// the standardised FP32 copies (the 7th input is the constant 1).
-__global__ void k_stats(const double* __restrict__ X, const double* __restrict__ Y, int64_t n,
-                        double* stats /* mean_in[6] sd_in[6] mean_out[7] sd_out[7] */) {
-    const int col = blockIdx.x;  // 0..5 inputs, 6..12 outputs
-    const double* src = col < 6 ? X : Y;
-    const int w = col < 6 ? 6 : 7, c = col < 6 ? col : col - 6;
+// Column means and standard deviations (FP64) of X[n x 6], Y[n x 7] and the
+// optional feature F[n], then the standardised FP32 copies (the 7th input is
+// the standardised feature, or the constant 1 without one).
+__global__ void k_stats(const double* __restrict__ X, const double* __restrict__ Y,
+                        const double* __restrict__ F, int64_t n,
+                        double* stats /* mean_in[6] sd_in[6] mean_out[7] sd_out[7] mean_f sd_f */) {
+    const int col = blockIdx.x;  // 0..5 inputs, 6..12 outputs, 13 the feature
+    if (col == 13 && !F) {
+        if (threadIdx.x == 0) {
+            stats[26] = 0.0;
+            stats[27] = 1.0;
+        }
+        return;
+    }
+    const double* src = col < 6 ? X : col < 13 ? Y : F;
+    const int w = col < 6 ? 6 : col < 13 ? 7 : 1, c = col < 6 ? col : col < 13 ? col - 6 : 0;
     double s = 0.0, s2 = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         const double v = src[i * w + c];
@@ -400,20 +410,24 @@ __global__ void k_stats(const double* __restrict__ X, const double* __restrict__
         if (col < 6) {
             stats[col] = mean;
             stats[6 + col] = sd;
-        } else {
+        } else if (col < 13) {
             stats[12 + c] = mean;
             stats[19 + c] = sd;
+        } else {
+            stats[26] = mean;
+            stats[27] = sd;
         }
     }
 }
 
-__global__ void k_standardise(const double* __restrict__ X, const double* __restrict__ Y, int64_t n,
+__global__ void k_standardise(const double* __restrict__ X, const double* __restrict__ Y,
+                              const double* __restrict__ F, int64_t n,
                               const double* __restrict__ st, float* __restrict__ Xs,
                               float* __restrict__ Ts) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         for (int k = 0; k < 6; ++k) Xs[i * DIN + k] = static_cast<float>((X[i * 6 + k] - st[k]) / st[6 + k]);
-        Xs[i * DIN + 6] = 1.f;
+        Xs[i * DIN + 6] = F ? static_cast<float>((F[i] - st[26]) / st[27]) : 1.f;
         if (Y)
             for (int k = 0; k < 7; ++k)
                 Ts[i * DOUT + k] = static_cast<float>((Y[i * 7 + k] - st[12 + k]) / st[19 + k]);
@@ -422,12 +436,12 @@ __global__ void k_standardise(const double* __restrict__ X, const double* __rest
 
 // Prediction: standardise the queries (zero-padded to B rows), and map the
 // network's outputs back to the log-likelihood and log-parameter partials.
-__global__ void k_predict_in(const double* __restrict__ q, int64_t m, int B, const double* __restrict__ st,
-                             float* __restrict__ X) {
+__global__ void k_predict_in(const double* __restrict__ q, const double* __restrict__ f, int64_t m,
+                             int B, const double* __restrict__ st, float* __restrict__ X) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
     for (int k = 0; k < 6; ++k) X[i * DIN + k] = i < m ? static_cast<float>((q[i * 6 + k] - st[k]) / st[6 + k]) : 0.f;
-    X[i * DIN + 6] = 1.f;
+    X[i * DIN + 6] = (f && i < m) ? static_cast<float>((f[i] - st[26]) / st[27]) : (f ? 0.f : 1.f);
 }
 
 __global__ void k_predict_out(const float* __restrict__ Y, int64_t m, const double* __restrict__ st,
@@ -461,8 +475,9 @@ struct hawkes_mlp {
     bf16 *W2b = nullptr, *W2Tb = nullptr;
     int64_t* step = nullptr;
     double* loss = nullptr;
-    double* stats = nullptr;  // 26 values
+    double* stats = nullptr;  // 28 values
     bool have_stats = false;
+    bool have_feature = false;  // the 7th input is a feature (else the constant 1)
     int64_t n = 0;
     float *Xs = nullptr, *Ts = nullptr;  // standardised data set
     // batch work buffers (BMAX rows)
@@ -564,7 +579,7 @@ int hawkes_mlp_create(hawkes_mlp** out, int device, void* cuda_stream, uint64_t 
         }
         if ((rc = alloc(&m->P, NPARAMS)) || (rc = alloc(&m->G, NPARAMS)) || (rc = alloc(&m->M, NPARAMS)) ||
             (rc = alloc(&m->V, NPARAMS)) || (rc = alloc(&m->W2b, DH * DH)) || (rc = alloc(&m->W2Tb, DH * DH)) ||
-            (rc = alloc(&m->step, 1)) || (rc = alloc(&m->loss, 1)) || (rc = alloc(&m->stats, 26)) ||
+            (rc = alloc(&m->step, 1)) || (rc = alloc(&m->loss, 1)) || (rc = alloc(&m->stats, 28)) ||
             (rc = alloc(&m->X, BMAX * DIN)) || (rc = alloc(&m->T, BMAX * DOUT)) ||
             (rc = alloc(&m->H1f, BMAX * DH)) || (rc = alloc(&m->H2f, BMAX * DH)) ||
             (rc = alloc(&m->Y, BMAX * DOUT)) || (rc = alloc(&m->dY, BMAX * DOUT)) ||
@@ -635,7 +650,8 @@ int hawkes_mlp_set_params(hawkes_mlp* m, const float* params) {
     return st_of(cudaStreamSynchronize(m->stream));
 }
 
-int hawkes_mlp_set_data(hawkes_mlp* m, int64_t n, const double* X, const double* Y) {
+int hawkes_mlp_set_data(hawkes_mlp* m, int64_t n, const double* X, const double* F,
+                        const double* Y) {
     HK_NVTX("hawkes_mlp_set_data");
     if (!m || n < 2 || !X || !Y) return HAWKES_ERR_ARG;
     DeviceGuard g(m->device);
@@ -643,26 +659,31 @@ int hawkes_mlp_set_data(hawkes_mlp* m, int64_t n, const double* X, const double*
     if (m->Xs) cudaFree(m->Xs);
     if (m->Ts) cudaFree(m->Ts);
     m->Xs = m->Ts = nullptr;
-    double *dX = nullptr, *dY = nullptr;
+    m->have_stats = false;
+    double *dX = nullptr, *dY = nullptr, *dF = nullptr;
     int rc = HAWKES_OK;
     if ((rc = alloc(&m->Xs, n * DIN)) || (rc = alloc(&m->Ts, n * DOUT)) || (rc = alloc(&dX, n * 6)) ||
-        (rc = alloc(&dY, n * 7))) {
+        (rc = alloc(&dY, n * 7)) || (F && (rc = alloc(&dF, n)))) {
         if (dX) cudaFree(dX);
         if (dY) cudaFree(dY);
+        if (dF) cudaFree(dF);
         return rc;
     }
     cudaStream_t st = m->stream;
     if ((rc = st_of(cudaMemcpyAsync(dX, X, n * 6 * sizeof(double), cudaMemcpyHostToDevice, st))) == HAWKES_OK &&
-        (rc = st_of(cudaMemcpyAsync(dY, Y, n * 7 * sizeof(double), cudaMemcpyHostToDevice, st))) == HAWKES_OK) {
-        k_stats<<<13, 256, 0, st>>>(dX, dY, n, m->stats);
-        k_standardise<<<256, 256, 0, st>>>(dX, dY, n, m->stats, m->Xs, m->Ts);
+        (rc = st_of(cudaMemcpyAsync(dY, Y, n * 7 * sizeof(double), cudaMemcpyHostToDevice, st))) == HAWKES_OK &&
+        (!F || (rc = st_of(cudaMemcpyAsync(dF, F, n * sizeof(double), cudaMemcpyHostToDevice, st))) == HAWKES_OK)) {
+        k_stats<<<14, 256, 0, st>>>(dX, dY, dF, n, m->stats);
+        k_standardise<<<256, 256, 0, st>>>(dX, dY, dF, n, m->stats, m->Xs, m->Ts);
         rc = st_of(cudaStreamSynchronize(st));
     }
     cudaFree(dX);
     cudaFree(dY);
+    if (dF) cudaFree(dF);
     if (rc != HAWKES_OK) return rc;
     m->n = n;
     m->have_stats = true;
+    m->have_feature = F != nullptr;
     return HAWKES_OK;
 }
 
@@ -707,27 +728,28 @@ int hawkes_mlp_loss_grad(hawkes_mlp* m, int batch, const float* Xs, const float*
     return take_err(m);
 }
 
-int hawkes_mlp_predict(hawkes_mlp* m, int64_t count, const double* d_logp, double* d_out) {
+int hawkes_mlp_predict(hawkes_mlp* m, int64_t count, const double* d_logp, const double* d_feature,
+                       double* d_out) {
     HK_NVTX("hawkes_mlp_predict");
     if (!m || count < 1 || count > BMAX || !d_logp || !d_out || !hk::aligned8(d_logp) ||
-        !hk::aligned8(d_out))
+        !hk::aligned8(d_out) || !hk::aligned8(d_feature))
         return HAWKES_ERR_ARG;
-    if (!m->have_stats) return HAWKES_ERR_STATE;
+    if (!m->have_stats || (d_feature != nullptr) != m->have_feature) return HAWKES_ERR_STATE;
     DeviceGuard g(m->device);
     const int B = static_cast<int>((count + 63) / 64 * 64);
-    k_predict_in<<<(B + 255) / 256, 256, 0, m->stream>>>(d_logp, count, B, m->stats, m->X);
+    k_predict_in<<<(B + 255) / 256, 256, 0, m->stream>>>(d_logp, d_feature, count, B, m->stats, m->X);
     HM_TRY(forward_backward(m, B, false));
     k_predict_out<<<static_cast<int>((count * DOUT + 255) / 256), 256, 0, m->stream>>>(m->Y, count, m->stats,
                                                                                      d_out);
     return st_of(cudaGetLastError());
 }
 
-int hawkes_mlp_stats(hawkes_mlp* m, double* stats26) {
+int hawkes_mlp_stats(hawkes_mlp* m, double* stats28) {
     HK_NVTX("hawkes_mlp_stats");
-    if (!m || !stats26) return HAWKES_ERR_ARG;
+    if (!m || !stats28) return HAWKES_ERR_ARG;
     if (!m->have_stats) return HAWKES_ERR_STATE;
     DeviceGuard g(m->device);
-    HM_CUDA(cudaMemcpyAsync(stats26, m->stats, 26 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    HM_CUDA(cudaMemcpyAsync(stats28, m->stats, 28 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     return st_of(cudaStreamSynchronize(m->stream));
 }
 

@@ -107,12 +107,12 @@ _SIGS = {
     "hawkes_mlp_destroy": (None, [_VP]),
     "hawkes_mlp_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "hawkes_mlp_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
-    "hawkes_mlp_set_data": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D]),
+    "hawkes_mlp_set_data": (ctypes.c_int, [_VP, ctypes.c_int64, _D, _D, _D]),
     "hawkes_mlp_train": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, _D]),
     "hawkes_mlp_loss_grad": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                             ctypes.POINTER(ctypes.c_float), _D, ctypes.POINTER(ctypes.c_float),
                                             ctypes.POINTER(ctypes.c_float)]),
-    "hawkes_mlp_predict": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP]),
+    "hawkes_mlp_predict": (ctypes.c_int, [_VP, ctypes.c_int64, _VP, _VP, _VP]),
     "hawkes_mlp_stats": (ctypes.c_int, [_VP, _D]),
     "hawkes_mlp_wait": (ctypes.c_int, [_VP]),
 }
@@ -459,10 +459,13 @@ class MLP:
         p = _f32(p)
         _check(lib().hawkes_mlp_set_params(self.m, p.ctypes.data_as(_F)), "hawkes_mlp_set_params")
 
-    def set_data(self, X, Y):
+    def set_data(self, X, Y, F=None):
+        """Training set: X[n x 6] log-parameters, Y[n x 7] targets, F[n] the
+        optional seventh-input feature (None: the constant 1)."""
         X = _f64(X).reshape(-1, 6)
         Y = _f64(Y).reshape(-1, 7)
-        _check(lib().hawkes_mlp_set_data(self.m, X.shape[0], _dp(X), _dp(Y)), "hawkes_mlp_set_data")
+        F = None if F is None else _f64(F).reshape(-1)
+        _check(lib().hawkes_mlp_set_data(self.m, X.shape[0], _dp(X), _dp(F), _dp(Y)), "hawkes_mlp_set_data")
 
     def train(self, steps, batch=512, lr=1e-3, seed=0):
         loss = ctypes.c_double()
@@ -481,13 +484,14 @@ class MLP:
                "hawkes_mlp_loss_grad")
         return loss.value, g, Y
 
-    def predict(self, d_logp, count, d_out):
-        """Device pointers: d_logp[count x 6] -> d_out[count x 7] (queued)."""
-        _check(lib().hawkes_mlp_predict(self.m, int(count), _VP(int(d_logp)), _VP(int(d_out))),
-               "hawkes_mlp_predict")
+    def predict(self, d_logp, count, d_out, d_feature=0):
+        """Device pointers: d_logp[count x 6] (and d_feature[count] when the
+        network was trained with a feature) -> d_out[count x 7] (queued)."""
+        _check(lib().hawkes_mlp_predict(self.m, int(count), _VP(int(d_logp)), _VP(int(d_feature) or None),
+                                        _VP(int(d_out))), "hawkes_mlp_predict")
 
     def stats(self):
-        s = np.zeros(26)
+        s = np.zeros(28)
         _check(lib().hawkes_mlp_stats(self.m, _dp(s)), "hawkes_mlp_stats")
         return s
 

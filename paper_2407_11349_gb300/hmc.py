@@ -27,6 +27,14 @@ the trajectory and the exact accept step keeps p(Theta | X, t) invariant;
 the shift removes the part of the X-dependence that is locally a change of
 slope.  Cost: one more exact evaluation per iteration (3 instead of 2).
 
+Draw feature (cut posterior).  Instead of a shift, the network can be told
+about the draw: its seventh input is z = ell_exact(a; X), the exact
+log-likelihood at a fixed anchor a under the iteration's locations (one more
+exact evaluation per iteration), and it is trained on (eta, z) -> (ell,
+grad) pairs recorded with their draw's z.  z depends on X and a only, so the
+field is again fixed for the whole trajectory and the exact accept step
+keeps p(Theta | X, t) invariant.
+
 Chains advance in lockstep: the exact evaluations of all chains are one
 batched launch (``Batch``), the surrogate's predictions one network call.
 Step size: dual averaging (Hoffman and Gelman 2014); metric: a dense
@@ -90,6 +98,7 @@ class HawkesTarget:
             self.b_ev = Batch(self.hks, None, None, self.flags, s)
             self.b_rs.capture(self.dp.data_ptr(), self.dout.data_ptr())
             self.b_ev.capture(self.dp.data_ptr(), self.dout.data_ptr())
+        self.b_ll = None
         self.n_exact = 0
         self.n_events = ds.n
 
@@ -113,14 +122,16 @@ class HawkesTarget:
         self.n_exact += self.C
         return out[:, 0], out[:, 1:] * p
 
-    def _run_sequential(self, eta, iteration, resample):
+    def _run_sequential(self, eta, iteration, resample, loglik_only=False):
+        from .hawkes import HAWKES_LOGLIK_ONLY
         p = np.exp(np.asarray(eta, dtype=np.float64))
         out = np.full((self.C, 7), np.nan)
+        fl = self.flags | (HAWKES_LOGLIK_ONLY if loglik_only else 0)
         for c, h in enumerate(self.hks):
             try:
                 if resample:
                     h.resample(self.seed, c, iteration)
-                ll, g = h.loglik_grad(p[c], self.flags)
+                ll, g = h.loglik_grad(p[c], fl)
                 out[c, 0], out[c, 1:] = ll, g
             except self.HawkesError:
                 self.n_failed += 1
@@ -137,18 +148,47 @@ class HawkesTarget:
             return self._run_sequential(eta, 0, False)
         return self._run(self.b_ev, eta, 0)
 
+    def _ll_batches(self):
+        """Batches with the log-likelihood-only flag (built on first use)."""
+        if self.b_ll is None:
+            from .hawkes import HAWKES_LOGLIK_ONLY, Batch
+            s = self.stream.cuda_stream
+            fl = self.flags | HAWKES_LOGLIK_ONLY
+            self.b_ll = (Batch(self.hks, [self.seed] * self.C, list(range(self.C)), fl, s),
+                         Batch(self.hks, None, None, fl, s))
+            for b in self.b_ll:
+                b.capture(self.dp.data_ptr(), self.dout.data_ptr())
+        return self.b_ll
+
+    def resample_eval_loglik(self, iteration, eta):
+        """As resample_eval, log-likelihood only (its gradient is NaN): the
+        sweep forms two moment sums per row instead of six."""
+        if self.sequential:
+            return self._run_sequential(eta, iteration, True, loglik_only=True)
+        return self._run(self._ll_batches()[0], eta, iteration)
+
+    def eval_loglik(self, eta):
+        if self.sequential:
+            return self._run_sequential(eta, 0, False, loglik_only=True)
+        return self._run(self._ll_batches()[1], eta, 0)
+
     def close(self):
         if not self.sequential:
             self.b_rs.close()
             self.b_ev.close()
+        if self.b_ll is not None:
+            for b in self.b_ll:
+                b.close()
         for h in self.hks:
             h.close()
 
 
 class SurrogateField:
-    """The network's (log-likelihood, eta-gradient) prediction for C chains."""
+    """The network's (log-likelihood, eta-gradient) prediction for C chains.
+    feature=True: the network was trained with a seventh-input feature, and
+    ``set_feature`` gives each chain's value for the coming trajectory."""
 
-    def __init__(self, mlp, n_chains, device=0):
+    def __init__(self, mlp, n_chains, device=0, feature=False):
         import torch
 
         self.torch = torch
@@ -156,13 +196,18 @@ class SurrogateField:
         self.C = n_chains
         self.dq = torch.zeros((n_chains, 6), dtype=torch.float64, device=f"cuda:{device}")
         self.dout = torch.zeros((n_chains, 7), dtype=torch.float64, device=f"cuda:{device}")
+        self.df = torch.zeros(n_chains, dtype=torch.float64, device=f"cuda:{device}") if feature else None
         self.n_calls = 0
+
+    def set_feature(self, z):
+        self.df.copy_(self.torch.from_numpy(np.asarray(z, dtype=np.float64)))
 
     def __call__(self, eta):
         torch = self.torch
         self.dq.copy_(torch.from_numpy(np.asarray(eta, dtype=np.float64)))
         torch.cuda.synchronize()
-        self.mlp.predict(self.dq.data_ptr(), self.C, self.dout.data_ptr())
+        self.mlp.predict(self.dq.data_ptr(), self.C, self.dout.data_ptr(),
+                         0 if self.df is None else self.df.data_ptr())
         self.mlp.wait()
         out = self.dout.cpu().numpy()
         self.n_calls += 1
@@ -215,7 +260,10 @@ class Sampler:
         self.jitter = float(jitter)  # step size drawn from eps * U(1 - jitter, 1 + jitter)
         self.iteration = 0
         self.divergent = 0
-        self.record = None  # list of (eta, loglik, grad) exact evaluations, when collecting
+        # list of (eta, loglik, grad, z) exact evaluations, when collecting; z
+        # is the draw feature of the evaluation's locations (None without one)
+        self.record = None
+        self.z = None
 
     def _exact(self, eta, resample=False):
         if resample:
@@ -223,7 +271,7 @@ class Sampler:
         else:
             ll, g = self.target.eval(eta)
         if self.record is not None:
-            self.record.append((eta.copy(), ll.copy(), g.copy()))
+            self.record.append((eta.copy(), ll.copy(), g.copy(), None if self.z is None else self.z.copy()))
         lp, gp = self.prior(eta)
         return ll + lp, g + gp
 
@@ -250,12 +298,15 @@ class Sampler:
     def _velocity(self, p):
         return np.einsum("cij,cj->ci", self.cov, p)
 
-    def transition(self, field=None, anchor=None, moves=1):
+    def transition(self, field=None, anchor=None, moves=1, feature_anchor=None):
         """One cut-posterior iteration: new locations, then `moves` HMC moves
         under them (the paper's scheme has one).  field(eta) -> (loglik, grad)
         drives the trajectories (None: exact).  anchor (6,) or (C, 6), with a
         field: shift the field by the exact minus the field's gradient at the
         anchor under this iteration's locations (see the module notes).
+        feature_anchor (6,) or (C, 6): evaluate the exact log-likelihood there
+        under the new locations as this iteration's draw feature z (recorded
+        with the exact evaluations, and given to a field that takes one).
         Every move under the same locations starts from the exact value of
         the state the previous move left, so a further surrogate move costs
         one exact evaluation.  A trajectory that leaves |eta| <= ETA_MAX or
@@ -263,7 +314,19 @@ class Sampler:
         use the current state instead).  Returns the acceptance probability
         of each chain, averaged over the moves."""
         self.iteration += 1
-        lp0, g0 = self._exact(self.q, resample=self.cut)
+        self.z = None
+        if feature_anchor is not None:
+            # the new locations, evaluated first at the anchor: this draw's feature
+            f_pt = np.array(np.broadcast_to(feature_anchor, self.q.shape), dtype=np.float64)
+            if self.cut:
+                self.z = self.target.resample_eval(self.iteration, f_pt)[0]
+            else:
+                self.z = self.target.eval(f_pt)[0]
+            if field is not None:
+                field.set_feature(self.z)
+            lp0, g0 = self._exact(self.q)
+        else:
+            lp0, g0 = self._exact(self.q, resample=self.cut)
         shift = 0.0
         if field is not None and anchor is not None:
             a_pt = np.array(np.broadcast_to(anchor, self.q.shape), dtype=np.float64)
@@ -324,7 +387,7 @@ class Sampler:
         g_new = np.where(take[:, None], g1, g0) if (g1 is not None and g0 is not None) else None
         return a, lp_new, g_new
 
-    def warmup(self, n, field=None, anchor=None, moves=1):
+    def warmup(self, n, field=None, anchor=None, moves=1, feature_anchor=None):
         """Adapt the step size (dual averaging, every iteration) and the dense
         metric: a fast window (first 15%), slow windows of doubling length
         whose draws give a covariance estimate (shrunk towards its diagonal),
@@ -340,7 +403,7 @@ class Sampler:
             b, w = e, 2 * w
         draws, last_start = [], start
         for k in range(n):
-            a = self.transition(field, anchor, moves)
+            a = self.transition(field, anchor, moves, feature_anchor)
             self.eps = da.update(a)
             for (w0, w1) in bounds:
                 if w0 <= k < w1:
@@ -359,12 +422,12 @@ class Sampler:
         self.eps = da.final()
         return last_start
 
-    def sample(self, n, field=None, anchor=None, moves=1):
+    def sample(self, n, field=None, anchor=None, moves=1, feature_anchor=None):
         out = np.zeros((self.C, n, 6))
         acc = np.zeros(n)
         t0 = time.perf_counter()
         for k in range(n):
-            acc[k] = self.transition(field, anchor, moves).mean()
+            acc[k] = self.transition(field, anchor, moves, feature_anchor).mean()
             out[:, k] = self.q
         return out, acc, time.perf_counter() - t0
 
@@ -390,7 +453,9 @@ class MHSampler:
     fresh location draw each iteration (cut scheme).  Each coordinate's
     proposal scale adapts during warmup towards an acceptance rate of 0.44
     (Robbins-Monro on its log).  Chains advance in lockstep: each univariate
-    update is one batched exact evaluation of all chains."""
+    update is one batched exact evaluation of all chains, of the
+    log-likelihood only when the target offers that (the sampler needs no
+    gradient)."""
 
     def __init__(self, target, prior, eta_init, seed=0, cut=True):
         self.target = target
@@ -401,12 +466,15 @@ class MHSampler:
         self.rng = np.random.default_rng(seed)
         self.log_scale = np.full((self.C, 6), np.log(0.01))
         self.iteration = 0
+        self.warm_k = 0  # warmup iterations done (the adaptation schedule's position)
 
     def _logpost(self, eta, resample=False):
+        ll_only = hasattr(self.target, "eval_loglik")
         if resample:
-            ll, _ = self.target.resample_eval(self.iteration, eta)
+            f = self.target.resample_eval_loglik if ll_only else self.target.resample_eval
+            ll, _ = f(self.iteration, eta)
         else:
-            ll, _ = self.target.eval(eta)
+            ll, _ = (self.target.eval_loglik if ll_only else self.target.eval)(eta)
         return ll + self.prior(eta)[0]
 
     def transition(self, adapt_rate=0.0):
@@ -431,18 +499,25 @@ class MHSampler:
         return acc
 
     def warmup(self, n):
-        for k in range(n):
-            self.transition(adapt_rate=1.0 / np.sqrt(k + 1.0))
+        """n more adaptation iterations, continuing the schedule (rate
+        1/sqrt(k + 1) at the k-th warmup iteration overall), so a run resumed
+        from a checkpoint taken during warmup adapts as an uninterrupted one."""
+        for _ in range(n):
+            self.transition(adapt_rate=1.0 / np.sqrt(self.warm_k + 1.0))
+            self.warm_k += 1
 
     # ---- checkpoint -----------------------------------------------------
     def state(self):
         return {"kind": "mh", "q": self.q.copy(), "log_scale": self.log_scale.copy(),
-                "iteration": self.iteration, "rng": self.rng.bit_generator.state}
+                "iteration": self.iteration, "warm_k": self.warm_k, "cut": self.cut,
+                "rng": self.rng.bit_generator.state}
 
     def set_state(self, st):
         self.q = np.array(st["q"], dtype=np.float64)
         self.log_scale = np.array(st["log_scale"], dtype=np.float64)
         self.iteration = int(st["iteration"])
+        self.warm_k = int(st.get("warm_k", 0))
+        self.cut = bool(st.get("cut", self.cut))
         self.rng.bit_generator.state = st["rng"]
 
     def sample(self, n):
@@ -478,52 +553,72 @@ def cut_posterior_reference(target, prior, q_start, cov, eps, rounds, burn, draw
     return np.concatenate(out, axis=0)
 
 
-def save(path, sampler, mlp=None, train_X=None, train_Y=None):
+def save(path, sampler, mlp=None, train_X=None, train_Y=None, train_F=None):
     """Checkpoint the sampler (HMC or univariate MH; and the surrogate:
-    weights + its training set, from which its standardisation is
-    recomputed) to an .npz file."""
+    weights + its training set, with the draw features of a network trained
+    on them, from which its standardisation is recomputed) to an .npz file.
+    The MH sampler has no surrogate: passing one with it raises ValueError."""
     import json
     st = sampler.state()
     if st.get("kind") == "mh":
+        if mlp is not None or train_X is not None or train_Y is not None or train_F is not None:
+            raise ValueError("the univariate MH sampler has no surrogate to save")
         np.savez(path, kind="mh", q=st["q"], log_scale=st["log_scale"], iteration=st["iteration"],
-                 rng=json.dumps(st["rng"]))
+                 warm_k=st["warm_k"], cut=st["cut"], rng=json.dumps(st["rng"]))
         return
     extra = {}
     if mlp is not None:
         extra["mlp_params"] = mlp.get_params()
         extra["train_X"] = np.asarray(train_X)
         extra["train_Y"] = np.asarray(train_Y)
+        if train_F is not None:
+            extra["train_F"] = np.asarray(train_F)
     np.savez(path, q=st["q"], eps=st["eps"], cov=st["cov"], iteration=st["iteration"], L=st["L"],
              jitter=st["jitter"], rng=json.dumps(st["rng"]), **extra)
 
 
 def load(path, sampler, mlp=None):
+    """Restore a checkpoint written by ``save`` into a sampler of the same
+    kind (and, for HMC, the surrogate).  A univariate MH checkpoint also
+    restores the sampler's cut setting; passing a surrogate with it raises
+    ValueError."""
     import json
     z = np.load(path, allow_pickle=False)
     if "kind" in z and str(z["kind"]) == "mh":
+        if mlp is not None:
+            raise ValueError("the univariate MH sampler has no surrogate to load")
         sampler.set_state({"q": z["q"], "log_scale": z["log_scale"], "iteration": int(z["iteration"]),
+                           "warm_k": int(z["warm_k"]) if "warm_k" in z else 0,
+                           "cut": bool(z["cut"]) if "cut" in z else sampler.cut,
                            "rng": json.loads(str(z["rng"]))})
         return
     sampler.set_state({"q": z["q"], "eps": z["eps"], "cov": z["cov"], "iteration": int(z["iteration"]),
                        "L": int(z["L"]), "jitter": float(z["jitter"]), "rng": json.loads(str(z["rng"]))})
     if mlp is not None and "mlp_params" in z:
-        mlp.set_data(z["train_X"], z["train_Y"])
+        mlp.set_data(z["train_X"], z["train_Y"], z["train_F"] if "train_F" in z else None)
         mlp.set_params(z["mlp_params"])
 
 
-def training_set(record, k_mad=25.0):
-    """Stack recorded exact evaluations into (X[n x 6], Y[n x 7]).  Rows with
-    a non-finite value, or with any column more than k_mad median absolute
-    deviations from that column's median, are dropped: leapfrog excursions
-    far outside the posterior (log-likelihoods many orders of magnitude
-    below the bulk) would otherwise set the network's standardisation."""
+def training_set(record, k_mad=25.0, with_feature=False):
+    """Stack recorded exact evaluations into (X[n x 6], Y[n x 7]), and with
+    with_feature also F[n], the draw feature of each evaluation (records
+    without one are skipped).  Rows with a non-finite value, or with any
+    column more than k_mad median absolute deviations from that column's
+    median, are dropped: leapfrog excursions far outside the posterior
+    (log-likelihoods many orders of magnitude below the bulk) would
+    otherwise set the network's standardisation."""
+    if with_feature:
+        record = [r for r in record if len(r) > 3 and r[3] is not None]
     X = np.concatenate([r[0] for r in record])
     Y = np.concatenate([np.column_stack([r[1], r[2]]) for r in record])
-    ok = np.all(np.isfinite(X), axis=1) & np.all(np.isfinite(Y), axis=1)
-    X, Y = X[ok], Y[ok]
-    Z = np.column_stack([X, Y])
+    F = np.concatenate([r[3] for r in record]) if with_feature else np.zeros(X.shape[0])
+    ok = np.all(np.isfinite(X), axis=1) & np.all(np.isfinite(Y), axis=1) & np.isfinite(F)
+    X, Y, F = X[ok], Y[ok], F[ok]
+    Z = np.column_stack([X, Y, F])
     med = np.median(Z, axis=0)
     mad = np.median(np.abs(Z - med), axis=0)
     mad = np.where(mad > 0, mad, np.maximum(np.abs(med), 1.0) * 1e-12)
     keep = np.all(np.abs(Z - med) <= k_mad * mad, axis=1)
+    if with_feature:
+        return X[keep], Y[keep], F[keep]
     return X[keep], Y[keep]

@@ -76,3 +76,44 @@ def test_surrogate_hmc_matches_exact_and_saves_exact_evaluations():
         net.close()
     finally:
         tgt.close()
+
+
+def test_cut_scheme_feature_surrogate_and_loglik_only_target():
+    """Under the cut scheme: the warmup records each location draw's feature
+    (the exact log-likelihood at a fixed anchor under that draw); a network
+    trained with it as its seventh input drives surrogate HMC with the
+    feature of each new draw, costing three exact evaluations per iteration
+    (anchor, start, end).  The target's log-likelihood-only evaluations give
+    the full ones' values (the univariate MH sampler uses them)."""
+    pytest.importorskip("torch")
+    ds = synth.clustered_dataset(4000, seed=43)
+    C, L = 4, 8
+    eta0 = np.log(synth.DEFAULT_PARAMS)
+    tgt = hmc.HawkesTarget(ds, C, seed=6)
+    try:
+        init = np.tile(eta0, (C, 1)) + np.random.default_rng(1).normal(0, 0.01, (C, 6))
+        ex = hmc.Sampler(tgt, hmc.Prior(eta0), init, n_leapfrog=L, seed=2, cut=True)
+        ex.record = []
+        last = ex.warmup(200, feature_anchor=eta0)
+        X, Y, F = hmc.training_set(ex.record[1 + last * (L + 1):], with_feature=True)
+        assert X.shape[0] == F.shape[0] > 0.8 * C * (200 - last) * (L + 1) and np.all(np.isfinite(F))
+        net = MLP(0, seed=4)
+        try:
+            net.set_data(X, Y, F)
+            net.train(2000, batch=256, lr=1e-3, seed=5)
+            field = hmc.SurrogateField(net, C, feature=True)
+            smp = hmc.Sampler(tgt, hmc.Prior(eta0), ex.q, n_leapfrog=L, seed=7, cut=True)
+            smp.eps, smp.iteration = ex.eps.copy(), ex.iteration
+            smp.set_cov(ex.cov)
+            n0 = tgt.n_exact
+            d, acc, _ = smp.sample(50, field=field, feature_anchor=eta0)
+            assert tgt.n_exact - n0 == 50 * C * 3
+            assert np.all(np.isfinite(d)) and acc.mean() > 0.05
+        finally:
+            net.close()
+        q = ex.q.copy()
+        ll_full, _ = tgt.eval(q)
+        ll_only, g = tgt.eval_loglik(q)
+        assert np.all(np.abs(ll_only - ll_full) <= 1e-7 * np.abs(ll_full)) and np.all(np.isnan(g))
+    finally:
+        tgt.close()

@@ -72,32 +72,45 @@ def test_training_fits_a_smooth_function():
         net.close()
 
 
-def test_predict_matches_reference_element_by_element():
+@pytest.mark.parametrize("feature", [False, True])
+def test_predict_matches_reference_element_by_element(feature):
     """hawkes_mlp_predict against the reference forward pass after the same
-    standardisation: inputs (q - mean_in) / sd_in with a constant 1 appended,
-    outputs mean_out + sd_out * y, with the network's stored weights and the
-    GPU's BF16 rounding points; every element within 2e-4 of its column's
-    output scale (sd_out)."""
+    standardisation: inputs (q - mean_in) / sd_in with the seventh input
+    appended (the constant 1, or the standardised feature (f - mean_f) /
+    sd_f), outputs mean_out + sd_out * y, with the network's stored weights
+    and the GPU's BF16 rounding points; every element within 2e-4 of its
+    column's output scale (sd_out)."""
     torch = pytest.importorskip("torch")
+    from paper_2407_11349_gb300.hawkes import HawkesError
     rng = np.random.default_rng(17)
     X = rng.normal(size=(500, 6)) * np.array([0.1, 0.2, 0.3, 0.1, 0.2, 0.4]) + np.log([0.5, 20, 7, 0.3, 0.2, 2])
     Y = np.column_stack([rng.normal(-1e6, 300.0, 500), rng.normal(0, 50.0, (500, 6))])
+    F = rng.normal(-1e6, 40.0, 500) if feature else None
     net = MLP(0, seed=9)
     try:
-        net.set_data(X, Y)
+        net.set_data(X, Y, F)
         net.train(200, batch=128, lr=1e-3, seed=2)
         theta = net.get_params().astype(np.float64)
         st = net.stats()
         q = X[:77] + rng.normal(0, 0.05, (77, 6))
+        f = F[:77] + rng.normal(0, 5.0, 77) if feature else None
         dq = torch.tensor(q, dtype=torch.float64, device="cuda")
+        df = torch.tensor(f, dtype=torch.float64, device="cuda") if feature else None
         dout = torch.zeros((77, 7), dtype=torch.float64, device="cuda")
-        net.predict(dq.data_ptr(), 77, dout.data_ptr())
+        with pytest.raises(HawkesError):  # the feature must be given exactly when trained with one
+            net.predict(dq.data_ptr(), 77, dout.data_ptr(), 0 if feature else dq.data_ptr())
+        net.predict(dq.data_ptr(), 77, dout.data_ptr(), df.data_ptr() if feature else 0)
         net.wait()
         got = dout.cpu().numpy()
     finally:
         net.close()
+    if feature:
+        assert abs(st[26] - F.mean()) < 1e-9 * abs(F.mean()) and abs(st[27] - F.std()) < 1e-6 * F.std()
+    else:
+        assert st[26] == 0.0 and st[27] == 1.0
     xs = (q - st[:6]) / st[6:12]
-    xin = np.column_stack([xs.astype(np.float32).astype(np.float64), np.ones(77)])
+    z = ((f - st[26]) / st[27]).astype(np.float32).astype(np.float64) if feature else np.ones(77)
+    xin = np.column_stack([xs.astype(np.float32).astype(np.float64), z])
     y, _ = mo.forward(theta, xin, bf16=True)
     want = st[12:19] + st[19:26] * y
     err = np.abs(got - want) / st[19:26]

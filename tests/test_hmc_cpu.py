@@ -249,3 +249,139 @@ def test_mh_checkpoint_resume_is_bit_identical(tmp_path):
     hmc.load(path, b)
     got = [b.transition().copy() for _ in range(12)]
     assert np.array_equal(np.stack(ref), np.stack(got)) and np.array_equal(a.q, b.q)
+
+
+def test_mh_checkpoint_during_warmup_resumes_the_adaptation(tmp_path):
+    """A run checkpointed partway through warmup, resumed into a sampler
+    built with a different cut setting, continues exactly as the
+    uninterrupted run (adaptation schedule, cut setting and RNG restored)."""
+    C = 3
+    a = hmc.MHSampler(GaussTarget(M, S, C), hmc.Prior(ETA0), np.tile(M, (C, 1)), seed=11)
+    a.warmup(12)
+    path = tmp_path / "mh_warm.npz"
+    hmc.save(path, a)
+    a.warmup(18)
+    ref = [a.transition().copy() for _ in range(6)]
+    b = hmc.MHSampler(GaussTarget(M, S, C), hmc.Prior(ETA0), np.zeros((C, 6)), seed=0, cut=False)
+    hmc.load(path, b)
+    assert b.cut is True and b.warm_k == 12
+    b.warmup(18)
+    got = [b.transition().copy() for _ in range(6)]
+    assert np.array_equal(a.log_scale, b.log_scale)
+    assert np.array_equal(np.stack(ref), np.stack(got)) and np.array_equal(a.q, b.q)
+
+
+def test_mh_checkpoint_rejects_a_surrogate(tmp_path):
+    C = 2
+    a = hmc.MHSampler(GaussTarget(M, S, C), hmc.Prior(ETA0), np.tile(M, (C, 1)), seed=1)
+    with pytest.raises(ValueError):
+        hmc.save(tmp_path / "x.npz", a, mlp=object())
+    hmc.save(tmp_path / "y.npz", a)
+    with pytest.raises(ValueError):
+        hmc.load(tmp_path / "y.npz", a, mlp=object())
+
+
+def test_mh_uses_the_loglik_only_evaluations_when_offered():
+    """A target with eval_loglik / resample_eval_loglik: the MH sampler calls
+    only those (it needs no gradient)."""
+    class LLOnly(GaussTarget):
+        def __init__(self, *a):
+            super().__init__(*a)
+            self.full_calls = 0
+
+        def eval(self, eta):
+            self.full_calls += 1
+            return super().eval(eta)
+
+        def resample_eval(self, it, eta):
+            self.full_calls += 1
+            return super().resample_eval(it, eta)
+
+        def eval_loglik(self, eta):
+            ll, g = GaussTarget.eval(self, eta)
+            return ll, np.full_like(g, np.nan)
+
+        def resample_eval_loglik(self, it, eta):
+            ll, g = GaussTarget.eval(self, eta)
+            return ll, np.full_like(g, np.nan)
+
+    C = 2
+    t = LLOnly(M, S, C)
+    a = hmc.MHSampler(t, hmc.Prior(ETA0), np.tile(M, (C, 1)), seed=3)
+    a.warmup(5)
+    a.sample(5)
+    assert t.full_calls == 0
+
+
+class SlopeDrawTarget(GaussTarget):
+    """Each location draw adds u (w . eta) to the log-likelihood, one scalar
+    u ~ N(0, 1.5^2) per chain and draw along a fixed direction w: the
+    draw-to-draw change of the surface has one degree of freedom."""
+
+    W = np.array([1.0, -0.5, 0.8, 0.3, -1.0, 0.6]) / 3.0
+
+    def __init__(self, m, s, C, seed=0):
+        super().__init__(m, s, C)
+        self.rng = np.random.default_rng(seed)
+        self.u = np.zeros(C)
+
+    def eval(self, eta):
+        ll, g = super().eval(eta)
+        return ll + self.u * (eta @ (self.W / S)), g + self.u[:, None] * (self.W / S)
+
+    def resample_eval(self, iteration, eta):
+        self.u = 1.5 * self.rng.standard_normal(self.C)
+        return self.eval(eta)
+
+
+class FeatureField:
+    """A surrogate that reads the draw from z = ell(a; X): here it knows the
+    surface's form, so the feature recovers u exactly."""
+
+    def __init__(self, anchor):
+        self.a = anchor
+        self.u = 0.0
+
+    def set_feature(self, z):
+        base = -0.5 * np.sum(((self.a - M) / S) ** 2)
+        self.u = (np.asarray(z) - base) / (self.a @ (SlopeDrawTarget.W / S))
+
+    def __call__(self, eta):
+        return None, -(eta - M) / S ** 2 + np.asarray(self.u)[:, None] * (SlopeDrawTarget.W / S)
+
+
+def test_draw_feature_raises_acceptance_under_the_cut_scheme_and_stays_exact():
+    """With the exact log-likelihood at a fixed anchor under each draw as the
+    field's input, the field follows the draw-to-draw change and acceptance
+    rises; the chains still sample the cut posterior (mean unchanged: the
+    slopes average out)."""
+    def plain(eta):  # the draw-averaged surface
+        return None, -(eta - M) / S ** 2
+
+    C = 4
+    acc, means = {}, {}
+    for name in ("plain", "feature"):
+        tgt = SlopeDrawTarget(M, S, C, seed=21)
+        smp = hmc.Sampler(tgt, hmc.Prior(ETA0), np.tile(M, (C, 1)) + 0.01, n_leapfrog=8, seed=22)
+        smp.warmup(300)
+        a_pt = M + 0.5 * S
+        if name == "plain":
+            d, a, _ = smp.sample(1500, plain)
+        else:
+            n0 = tgt.n_exact
+            d, a, _ = smp.sample(1500, FeatureField(a_pt), feature_anchor=a_pt)
+            assert tgt.n_exact - n0 == 1500 * C * 3  # anchor, start, end per iteration
+        acc[name], means[name] = a.mean(), d.reshape(-1, 6).mean(axis=0)
+        mu_post, var_post = posterior(M, S, ETA0)
+        assert np.all(np.abs(means[name] - mu_post) < 0.15 * S), (name, means[name], mu_post)
+    assert acc["feature"] > acc["plain"] + 0.1, acc
+
+
+def test_training_set_with_feature():
+    rec = [(np.zeros((2, 6)) + k, np.array([1.0, 2.0]) + k, np.ones((2, 6)), np.array([5.0, 6.0]) + k)
+           for k in range(5)] + [(np.zeros((2, 6)), np.zeros(2), np.ones((2, 6)), None)]
+    X, Y, F = hmc.training_set(rec, with_feature=True)
+    assert X.shape == (10, 6) and Y.shape == (10, 7) and F.shape == (10,)
+    assert np.array_equal(F[:2], [5.0, 6.0])
+    X2, Y2 = hmc.training_set(rec)
+    assert X2.shape[0] == 12
