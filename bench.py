@@ -208,7 +208,7 @@ def bench_batch(ds_c3, steps, warmup):
 
 
 def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, ref_rounds=0,
-              lite=False, flags=0):
+              lite=False, flags=0, moves=0, train_from="last", progress=None):
     """Min bulk ESS per second of exact HMC vs surrogate HMC, same data, same
     adapted step size and metric.  cut=True: locations resampled every
     iteration (the cut-posterior scheme); cut=False: locations held fixed,
@@ -220,7 +220,12 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     draw, and the paper's univariate Metropolis-Hastings.  ref_rounds > 0
     (cut only): every sampler is also compared with an independent sample
     of the cut posterior.  flags: extra likelihood flags (e.g. the exact
-    underflow skip, which changes no result)."""
+    underflow skip, which changes no result).  moves > 1 (lite runs): the
+    plain and (cut) feature surrogates also run with that many moves per
+    location draw.  train_from: "last" trains the network on the warmup's
+    evaluations from its last slow adaptation window on, "fast" on every
+    evaluation after the first fast window (15% of the warmup).  progress:
+    a file that receives each finished part as one JSON line."""
     from paper_2407_11349_gb300 import diagnostics as dg
     from paper_2407_11349_gb300 import hmc, synth
     from paper_2407_11349_gb300.hawkes import MLP
@@ -242,7 +247,9 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     t0 = time.perf_counter()
     last = ex.warmup(warmup, feature_anchor=a_f)
     t_warm = time.perf_counter() - t0
-    rec = ex.record[1 + last * (leapfrog + 1):]
+    n_warm_exact = tgt.n_exact
+    first = last if train_from == "last" else int(0.15 * warmup)
+    rec = ex.record[1 + first * (leapfrog + 1):]
     X, Y = hmc.training_set(rec)
     ex.record = None
     net = MLP(torch_device(), seed=2)
@@ -260,14 +267,25 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
         loss_f = net_f.train(4000, batch=512, lr=1e-3, seed=3)
         field_f = hmc.SurrogateField(net_f, chains, feature=True)
 
-    def run(sampler, **kw):
+    def note(part, val):
+        if progress:
+            with open(progress, "a") as f:
+                f.write(json.dumps({part: val}, default=float) + "\n")
+
+    note("warmup", {"seconds": t_warm, "exact_evals": n_warm_exact, "training_pairs": int(X.shape[0]),
+                    "train_loss": loss, "train_s": t_train})
+
+    def run(name, sampler, **kw):
         n0 = tgt.n_exact
         d, acc, sec = sampler.sample(draws, **kw)
         summ = dg.summary(d, hmc.NAMES)
         ess = min(v["bulk_ess"] for v in summ.values())
-        return summ, {"min_bulk_ess": ess, "seconds": sec, "ess_per_s": ess / sec,
-                      "accept": float(acc.mean()), "exact_evals": tgt.n_exact - n0,
-                      "exact_evals_per_ess": (tgt.n_exact - n0) / max(ess, 1e-9)}
+        r = {"min_bulk_ess": ess, "seconds": sec, "ess_per_s": ess / sec,
+             "accept": float(acc.mean()), "exact_evals": tgt.n_exact - n0,
+             "exact_evals_per_ess": (tgt.n_exact - n0) / max(ess, 1e-9),
+             "mean": {k: summ[k]["mean"] for k in hmc.NAMES}, "mcse": {k: summ[k]["mcse"] for k in hmc.NAMES}}
+        note(name, r)
+        return summ, r
 
     def hmc_sampler(seed):
         smp = hmc.Sampler(tgt, prior, q_start, n_leapfrog=leapfrog, seed=seed, cut=cut)
@@ -276,28 +294,37 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
         return smp
 
     summaries, res = {}, {}
-    summaries["exact"], res["exact"] = run(ex)
-    summaries["surrogate"], res["surrogate"] = run(hmc_sampler(5), field=field)
+    summaries["exact"], res["exact"] = run("exact", ex)
+    summaries["surrogate"], res["surrogate"] = run("surrogate", hmc_sampler(5), field=field)
     if cut:
         # the network told about each draw through its seventh input
-        summaries["surrogate_feature"], res["surrogate_feature"] = run(hmc_sampler(9), field=field_f,
+        summaries["surrogate_feature"], res["surrogate_feature"] = run("surrogate_feature", hmc_sampler(9), field=field_f,
                                                                        feature_anchor=a_f)
         res["surrogate_feature"]["train_loss"] = loss_f
+    if lite and moves > 1:
+        # several surrogate moves per location draw (1 + moves exact
+        # evaluations; the feature network adds the anchor's evaluation)
+        nm = f"surrogate_{moves}_moves"
+        summaries[nm], res[nm] = run(nm, hmc_sampler(8), field=field, moves=moves)
+        if cut:
+            nm = f"surrogate_feature_{moves}_moves"
+            summaries[nm], res[nm] = run(nm, hmc_sampler(10), field=field_f, feature_anchor=a_f,
+                                         moves=moves)
     if not lite:
         # the anchored surrogate: each iteration's field is shifted by the
         # exact minus the network's gradient at a fixed anchor (the median of
         # the training points) under that iteration's locations
         summaries["surrogate_anchored"], res["surrogate_anchored"] = run(
-            hmc_sampler(7), field=field, anchor=np.median(X, axis=0))
+            "surrogate_anchored", hmc_sampler(7), field=field, anchor=np.median(X, axis=0))
         # three surrogate moves per location draw (1 + 3 exact evaluations)
-        summaries["surrogate_3_moves"], res["surrogate_3_moves"] = run(hmc_sampler(8), field=field,
+        summaries["surrogate_3_moves"], res["surrogate_3_moves"] = run("surrogate_3_moves", hmc_sampler(8), field=field,
                                                                        moves=3)
         # the paper's sampler: univariate Metropolis-Hastings, same target and start
         mh = hmc.MHSampler(tgt, prior, q_start, seed=6, cut=cut)
         mh.iteration = ex.iteration
         mh.log_scale = np.log(np.sqrt(np.stack([np.diag(c) for c in cov]))) + np.log(2.38 / np.sqrt(6.0))
         mh.warmup(50)
-        summaries["univariate_mh"], res["univariate_mh"] = run(mh)
+        summaries["univariate_mh"], res["univariate_mh"] = run("univariate_mh", mh)
     s_ex = summaries["exact"]
     for k, summ in summaries.items():
         res[k]["ess_per_s_vs_exact"] = res[k]["ess_per_s"] / res["exact"]["ess_per_s"]
@@ -327,8 +354,10 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     if net_f is not None:
         net_f.close()
     tgt.close()
+    note("cut_posterior_reference", ref)
     out = {"n_events": ds.n, "chains": chains, "leapfrog": leapfrog, "warmup_iters": warmup,
            "draws_per_chain": draws, "training_pairs": int(X.shape[0]), "train_loss": loss,
+           "warmup_exact_evals": n_warm_exact, "train_from": train_from,
            **res,
            "speedup_ess_per_s": res["surrogate"]["ess_per_s_vs_exact"],
            # at large N, where the exact evaluations dominate the time, the
@@ -506,6 +535,13 @@ def main():
     ap.add_argument("--mh-draws", type=int, default=400)
     ap.add_argument("--hmc-ref-rounds", type=int, default=0,
                     help="with --hmc-only: location draws per chain of the cut-posterior reference")
+    ap.add_argument("--hmc-moves", type=int, default=0,
+                    help="with --hmc-only: also run the surrogates with this many moves per location draw")
+    ap.add_argument("--hmc-train-from", default="last", choices=["last", "fast"],
+                    help="with --hmc-only: train on the warmup from its last slow window (last) or after "
+                         "its first fast window (fast)")
+    ap.add_argument("--hmc-progress", default=None,
+                    help="with --hmc-only: append each finished part to this file as a JSON line")
     ap.add_argument("--hmc-chains", type=int, default=4)
     ap.add_argument("--hmc-warmup", type=int, default=300)
     ap.add_argument("--hmc-draws", type=int, default=300)
@@ -545,6 +581,7 @@ def main():
         torch.cuda.set_stream(torch.cuda.Stream())
         r = bench_hmc(args.hmc_n, cut=not args.hmc_fixed, chains=args.hmc_chains, warmup=args.hmc_warmup,
                       draws=args.hmc_draws, lite=True, ref_rounds=args.hmc_ref_rounds,
+                      moves=args.hmc_moves, train_from=args.hmc_train_from, progress=args.hmc_progress,
                       flags=HAWKES_SKIP_SPATIAL if args.hmc_spatial else HAWKES_SKIP_UNDERFLOW)
         print(json.dumps({"hmc_only": r}))
         return
