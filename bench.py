@@ -157,6 +157,7 @@ def bench_batch(ds_c3, steps, warmup):
     dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
     b = Batch(hks, seeds, streams, HAWKES_F32, stream.cuda_stream)
     variant, chunk, order, tune_ms = b.tune(dp.data_ptr(), dout.data_ptr(), reps=1)
+    kc, n_groups = b.config()[3:]
     b.capture(dp.data_ptr(), dout.data_ptr())
     ev = lambda: torch.cuda.Event(enable_timing=True)
     douts = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
@@ -189,6 +190,13 @@ def bench_batch(ds_c3, steps, warmup):
         ts.append(sequential(100 + k))
     batch_out, seq_last = dout.cpu().numpy(), douts.cpu().numpy()
     agree = float(np.max(np.abs(seq_last[:, 0] - batch_out[:, 0]) / np.abs(seq_last[:, 0])))
+    # the same batch with one chain per CTA (the tuned k = 1 configuration)
+    t1 = []
+    if kc > 1:
+        b.set_chains_per_cta(1)
+        b.capture(dp.data_ptr(), dout.data_ptr())
+        batched(200)
+        t1 = [batched(201 + k) for k in range(3)]
     b.close()
     for h in hks:
         h.close()
@@ -200,10 +208,13 @@ def bench_batch(ds_c3, steps, warmup):
             "ms_per_step": mb, "ms_per_step_all": [round(v, 2) for v in tb],
             "sequential_ms_per_step": ms_, "sequential_ms_all": [round(v, 2) for v in ts],
             "problems": P, "pairs_per_step": pairs,
-            "tuned": {"variant": variant, "chunk_tiles": chunk, "order": order, "sweep_ms": tune_ms},
+            "tuned": {"variant": variant, "chunk_tiles": chunk, "order": order, "sweep_ms": tune_ms,
+                      "chains_per_cta": kc, "groups": n_groups},
+            "one_chain_per_cta_ms_per_step": statistics.median(t1) if t1 else None,
             "graph": True, "loglik_rel_diff_batch_vs_sequential": agree,
             "config": "30 chains x N=250,000 (own params, own resample stream) + 16 regional subsets "
-                      "N=5,000..200,000 (sum 899,416); one persistent launch in a CUDA graph; "
+                      "N=5,000..200,000 (sum 899,416); one persistent launch per kernel family in a "
+                      "CUDA graph (chains sharing their times swept chains_per_cta at a time); "
                       "medians of alternating batched / sequential repeats"}
 
 
@@ -831,6 +842,7 @@ def main():
             out["batch30"] = bt
             out["batch30_speedup"] = bt["speedup_vs_sequential"]
             out["batch30_speedup_min_max"] = [bt["speedup_min"], bt["speedup_max"]]
+            out["batch30_chains_per_cta"] = bt["tuned"]["chains_per_cta"]
         if world == 1 and args.hmc_n > 0 and args.workload == "c3":
             out["hmc"] = {"cut_posterior": bench_hmc(args.hmc_n, cut=True, ref_rounds=args.hmc_cut_reference),
                           "fixed_locations": bench_hmc(args.hmc_n, cut=False)}

@@ -401,19 +401,50 @@ int hawkes_batch_wait(hawkes_batch* batch);
 
 /*
  * Autotune the batch over the sweep variant, the column-chunk length of a
- * work item (16, 32 or 64 tiles of 256 sources) and the item order (0: all
+ * work item (16, 32 or 64 tiles of 256 sources), the item order (0: all
  * items longest first; 1: problem by problem, largest problem first, each
- * longest first).  Each configuration's single sweep launch is timed `reps`
- * times with CUDA events after a warm-up, at d_params / d_out (device
- * pointers as for hawkes_batch_run); the fastest is kept.  Outputs
- * (optional): the chosen variant, chunk length, order and mean sweep time in
- * ms.  Drops a captured graph (capture again after tuning).
+ * longest first) and the chains per CTA (1, 2 or 4; see
+ * hawkes_batch_set_chains_per_cta).  Each configuration's sweep launches
+ * are timed `reps` times with CUDA events after a warm-up, at d_params /
+ * d_out (device pointers as for hawkes_batch_run); the fastest is kept.
+ * Outputs (optional): the chosen variant, chunk length, order and mean sweep
+ * time in ms (hawkes_batch_get_config also gives the chains per CTA).  Drops
+ * a captured graph (capture again after tuning).
  */
 int hawkes_batch_tune(hawkes_batch* batch, const hawkes_params* d_params, double* d_out, int reps,
                       int* variant, int* chunk, int* order, double* best_ms);
 
 /* Select the sweep variant, chunk length and item order directly (drops a captured graph). */
 int hawkes_batch_set_config(hawkes_batch* batch, int variant, int chunk, int order);
+
+/*
+ * Chains per CTA.  MCMC chains of one data set (Sec. 3.2 runs 30) share their
+ * event times and differ in their location draws (Sec. 2.2) and parameters.
+ * With chains_per_cta = k > 1, the problems of the batch whose event times
+ * are identical (same n, bit-identical times; found when the batch is made)
+ * are split, in batch order, into groups of k, and each group is swept by a
+ * kernel whose CTAs take one row tile of the shared event order for all k
+ * chains at once: one TMA copy stages the column tile of all k chains, and
+ * each pair's time difference is formed once for the k chains.  Problems left
+ * over (other event times, or the remainder of a class) are swept one per
+ * item as with k = 1.  Results equal those of k = 1 up to FP32 rounding.
+ *   chains_per_cta  1, 2 or 4; k > 1 only with the space-time background's
+ *                   full gradient (not with HAWKES_BG_TIME, HAWKES_LOGLIK_ONLY
+ *                   or HAWKES_SKIP_UNDERFLOW): HAWKES_ERR_ARG otherwise
+ * Keeps the variant, chunk length and order; drops a captured graph.  The
+ * group kernel's tile buffer (104 B per event and chain pair at k = 2) is
+ * allocated here.
+ */
+int hawkes_batch_set_chains_per_cta(hawkes_batch* batch, int chains_per_cta);
+
+/*
+ * The batch's current configuration (outputs optional): sweep variant, chunk
+ * length, item order, chains per CTA, and the number of groups swept with
+ * several chains per CTA (0 when chains_per_cta is 1 or no k problems share
+ * their times).
+ */
+int hawkes_batch_get_config(const hawkes_batch* batch, int* variant, int* chunk, int* order,
+                            int* chains_per_cta, int* n_groups);
 
 /*
  * As hawkes_batch_tune, through the autotuner cache (see hawkes_tune_cached

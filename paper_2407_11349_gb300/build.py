@@ -17,8 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libhawkes.so")
 LIB_DEBUG = os.path.join(LIBDIR, "libhawkes_debug.so")  # -DHAWKES_DEBUG: device index checks
-SOURCES = ["sweep.cu", "sweep_bgt.cu", "sweep_ll.cu", "sweep_spatial.cu", "api.cu", "kernels.cu", "batch.cu", "mlp.cu", "noalloc.cu",
-           "tune_cache.cu"]
+SOURCES = ["sweep.cu", "sweep_bgt.cu", "sweep_ll.cu", "sweep_spatial.cu", "sweep_group.cu", "api.cu", "kernels.cu",
+           "batch.cu", "mlp.cu", "noalloc.cu", "tune_cache.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -732,8 +732,9 @@ int hawkes_profile_read(hawkes_ctx* c, hawkes_profile* out) {
 
 namespace hk {
 int tune_cache_get(const char* path, const char* key, int* variant, int* chunk, int* order,
-                   double* ms);
-int tune_cache_put(const char* path, const char* key, int variant, int chunk, int order, double ms);
+                   double* ms, int* kc);
+int tune_cache_put(const char* path, const char* key, int variant, int chunk, int order, double ms,
+                   int kc);
 int log2_ceil(double v);
 std::string device_key();
 }  // namespace hk
@@ -753,7 +754,7 @@ int hawkes_tune_cached(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, in
     const std::string key = dk + "single|n<=2^" + std::to_string(log2_ceil(static_cast<double>(c->n))) +
                             "|flags=" + std::to_string(flags);
     int v = -1;
-    if (tune_cache_get(cache_path, key.c_str(), &v, nullptr, nullptr, nullptr) == 1) {
+    if (tune_cache_get(cache_path, key.c_str(), &v, nullptr, nullptr, nullptr, nullptr) == 1) {
         HK_TRY(select_variant(c, v));
         if (chosen) *chosen = v;
         if (from_cache) *from_cache = 1;
@@ -763,7 +764,7 @@ int hawkes_tune_cached(hawkes_ctx* c, const hawkes_params* p, uint32_t flags, in
     HK_TRY(hawkes_tune(c, p, flags, reps, &v, ms.data()));
     if (chosen) *chosen = v;
     if (from_cache) *from_cache = 0;
-    return tune_cache_put(cache_path, key.c_str(), v, CHUNK, 0, ms[v]);
+    return tune_cache_put(cache_path, key.c_str(), v, CHUNK, 0, ms[v], 1);
 }
 
 int hawkes_debug_build(void) { return kDebug ? 1 : 0; }

@@ -104,6 +104,22 @@ struct ProbDesc {
     int64_t n, npad;
 };
 
+// A group of chains with identical event times, swept kc at a time by the
+// group kernel (sweep_group.cu): the group's tile records (TC / 2 + 3 kc TC
+// float4 per tile of TC events: the shared time plane, then three planes per
+// chain), the shared tie ranges and time bases, and each chain's per-call
+// constants and FP64 moment accumulators.
+constexpr int KMAX = 4;
+__host__ __device__ constexpr int gt_f4(int kc) { return TC / 2 + 3 * kc * TC; }
+struct GroupDesc {
+    const float4* tiles;
+    const int32_t* lo;
+    const double* tb;
+    const double* cc[KMAX];
+    double* acc[KMAX];
+    int64_t n, npad;
+};
+
 // Per-call constants, computed on the device from the parameters.
 enum {
     CC_KX = 0,      // sqrt(a_x)

@@ -5,12 +5,13 @@
 // The file is written by this library as a JSON object with one entry per
 // line:
 //   {
-//   "NVIDIA GB300|sm_103|single|n<=2^20|flags=0": {"variant": 0, "chunk": 16, "order": 0, "ms": 365.359, "nvariants": 5},
+//   "NVIDIA GB300|sm_103|single|n<=2^20|flags=0": {"variant": 0, "chunk": 16, "order": 0, "ms": 365.359, "nvariants": 5, "kc": 1},
 //   ...
 //   }
 // The reader accepts exactly that shape and skips any line it cannot parse,
 // so a damaged file degrades to cache misses, never to an error.  Entries
 // written by a build with a different number of sweep variants are ignored.
+// "kc" (chains per CTA of a batch's group sweep) may be absent, meaning 1.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -28,7 +29,7 @@ namespace {
 
 struct Entry {
     std::string key;
-    int variant = -1, chunk = 0, order = 0, nvariants = 0;
+    int variant = -1, chunk = 0, order = 0, nvariants = 0, kc = 1;
     double ms = 0.0;
 };
 
@@ -81,6 +82,9 @@ bool parse_line(const std::string& line, Entry* e) {
     e->order = static_cast<int>(o);
     e->ms = ms;
     e->nvariants = static_cast<int>(nv);
+    double kc = 1.0;
+    if (field(b, en, "kc", &kc) && !(kc >= 1.0 && kc <= 64.0)) return false;
+    e->kc = static_cast<int>(kc);
     return key_ok(e->key.c_str());
 }
 
@@ -109,7 +113,7 @@ std::vector<Entry> read_all(const char* path) {
 
 // 1: found (outputs written), 0: absent, HAWKES_ERR_ARG: bad arguments.
 int tune_cache_get(const char* path, const char* key, int* variant, int* chunk, int* order,
-                   double* ms) {
+                   double* ms, int* kc) {
     if (!path || !key_ok(key)) return HAWKES_ERR_ARG;
     const int nv = sweep_num_variants();
     int found = 0;
@@ -119,6 +123,7 @@ int tune_cache_get(const char* path, const char* key, int* variant, int* chunk, 
         if (chunk) *chunk = e.chunk;
         if (order) *order = e.order;
         if (ms) *ms = e.ms;
+        if (kc) *kc = e.kc;
         found = 1;  // the last valid entry for a key wins
     }
     return found;
@@ -126,9 +131,10 @@ int tune_cache_get(const char* path, const char* key, int* variant, int* chunk, 
 
 // Insert or replace an entry; the file is rewritten through a temporary file
 // and renamed into place, so readers never see a half-written file.
-int tune_cache_put(const char* path, const char* key, int variant, int chunk, int order, double ms) {
+int tune_cache_put(const char* path, const char* key, int variant, int chunk, int order, double ms,
+                   int kc) {
     if (!path || !key_ok(key) || variant < 0 || variant >= sweep_num_variants() || chunk < 0 ||
-        order < 0 || !(ms >= 0.0))
+        order < 0 || !(ms >= 0.0) || kc < 1 || kc > 64)
         return HAWKES_ERR_ARG;
     std::vector<Entry> all = read_all(path);
     Entry n;
@@ -138,6 +144,7 @@ int tune_cache_put(const char* path, const char* key, int variant, int chunk, in
     n.order = order;
     n.ms = ms;
     n.nvariants = sweep_num_variants();
+    n.kc = kc;
     bool replaced = false;
     for (Entry& e : all)
         if (e.key == n.key) {
@@ -153,8 +160,8 @@ int tune_cache_put(const char* path, const char* key, int variant, int chunk, in
         const Entry& e = all[k];
         ok = std::fprintf(f,
                           "\"%s\": {\"variant\": %d, \"chunk\": %d, \"order\": %d, \"ms\": %.3f, "
-                          "\"nvariants\": %d}%s\n",
-                          e.key.c_str(), e.variant, e.chunk, e.order, e.ms, e.nvariants,
+                          "\"nvariants\": %d, \"kc\": %d}%s\n",
+                          e.key.c_str(), e.variant, e.chunk, e.order, e.ms, e.nvariants, e.kc,
                           k + 1 < all.size() ? "," : "") > 0;
     }
     ok = ok && std::fputs("}\n", f) >= 0;
@@ -191,10 +198,10 @@ std::string device_key() {
 
 extern "C" int hawkes_tune_cache_get(const char* cache_path, const char* key, int* variant,
                                      int* chunk, int* order, double* ms) {
-    return hk::tune_cache_get(cache_path, key, variant, chunk, order, ms);
+    return hk::tune_cache_get(cache_path, key, variant, chunk, order, ms, nullptr);
 }
 
 extern "C" int hawkes_tune_cache_put(const char* cache_path, const char* key, int variant,
                                      int chunk, int order, double ms) {
-    return hk::tune_cache_put(cache_path, key, variant, chunk, order, ms);
+    return hk::tune_cache_put(cache_path, key, variant, chunk, order, ms, 1);
 }

@@ -100,6 +100,8 @@ _SIGS = {
     "hawkes_batch_tune": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _D]),
     "hawkes_batch_set_config": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "hawkes_batch_set_chains_per_cta": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "hawkes_batch_get_config": (ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int)] * 5),
     "hawkes_batch_tune_cached": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_char_p,
                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
@@ -385,6 +387,17 @@ def hawkes_batch_set_config(b, variant, chunk, order=1):
     _check(lib().hawkes_batch_set_config(b, int(variant), int(chunk), int(order)), "hawkes_batch_set_config")
 
 
+def hawkes_batch_set_chains_per_cta(b, chains_per_cta):
+    _check(lib().hawkes_batch_set_chains_per_cta(b, int(chains_per_cta)), "hawkes_batch_set_chains_per_cta")
+
+
+def hawkes_batch_get_config(b):
+    """(variant, chunk, order, chains_per_cta, n_groups) of the batch."""
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(lib().hawkes_batch_get_config(b, *[ctypes.byref(x) for x in v]), "hawkes_batch_get_config")
+    return tuple(x.value for x in v)
+
+
 class Batch:
     """Many contexts evaluated in one persistent sweep launch (optionally a CUDA graph)."""
 
@@ -417,6 +430,13 @@ class Batch:
 
     def set_config(self, variant, chunk, order=1):
         hawkes_batch_set_config(self.b, variant, chunk, order)
+
+    def set_chains_per_cta(self, k):
+        hawkes_batch_set_chains_per_cta(self.b, k)
+
+    def config(self):
+        """(variant, chunk, order, chains_per_cta, n_groups)."""
+        return hawkes_batch_get_config(self.b)
 
     def tune_cached(self, d_params, d_out, cache_path, reps=1):
         return hawkes_batch_tune_cached(self.b, d_params, d_out, cache_path, reps)

@@ -220,3 +220,108 @@ def test_batch_with_underflow_skip(problems):
             _close(got[p], *ref[p], f"skip graph problem {p}")
     finally:
         b.close()
+
+
+# ---------------------------------------------------------------------------
+# Several chains per CTA (problems with identical event times swept together)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kc,graph", [(2, False), (2, True), (4, False), (4, True)])
+def test_chains_per_cta_matches_oracle(problems, kc, graph):
+    """The four chains share their event times, so k = 2 makes two groups and
+    k = 4 one; the regional subsets are swept one per item.  Every problem's
+    outputs against the oracle on its own location draw, and against the
+    batch with one chain per CTA on the same draws."""
+    import oracle
+    torch, dss, params, hks, seeds, streams = problems
+    P = len(dss)
+    dp = torch.tensor(params, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+    b = Batch(hks, seeds, streams, HAWKES_F32)
+    try:
+        b.set_chains_per_cta(kc)
+        assert b.config()[3:] == (kc, 4 // kc)
+        if graph:
+            b.capture(dp.data_ptr(), dout.data_ptr())
+        torch.cuda.synchronize()
+        b.run(dp.data_ptr(), 23, dout.data_ptr())
+        b.wait()
+        got = dout.cpu().numpy()
+        b.set_chains_per_cta(1)
+        assert b.config()[3:] == (1, 0)
+        b.run(dp.data_ptr(), 23, dout.data_ptr())
+        b.wait()
+        one = dout.cpu().numpy()
+    finally:
+        b.close()
+    for p in range(P):
+        x, y = hks[p].locations()
+        ref, rows = oracle.loglik_grad(dss[p].t, x, y, params[p], s=dss[p].s, rows=True)
+        _close(got[p], ref, rows, f"k={kc} {'graph' if graph else 'eager'} problem {p} vs oracle")
+        _close(got[p], one[p], rows, f"k={kc} vs k=1 problem {p}")
+
+
+def test_chains_per_cta_remainder_model1_and_invalid_member():
+    """Three chains of one data set and one other problem at k = 2 (Model 1):
+    one group of two, the third chain and the other problem one per item.
+    Then a group member with invalid parameters: its outputs are NaN and the
+    error is reported, its group partner is unaffected."""
+    import oracle
+    from paper_2407_11349_gb300.hawkes import HAWKES_MODEL1
+    torch = pytest.importorskip("torch")
+    base = synth.voronoi_dataset(9_000, n_cells=200, seed=41)
+    other = synth.voronoi_dataset(4_321, n_cells=100, seed=42)
+    dss = [base, base, base, other]
+    params = synth.chain_params(4, seed=43)
+    hks = [Hawkes(0).load(ds) for ds in dss]
+    fl = HAWKES_F32 | HAWKES_MODEL1
+    dp = torch.tensor(params, dtype=torch.float64, device="cuda")
+    dout = torch.zeros((4, 7), dtype=torch.float64, device="cuda")
+    b = Batch(hks, [5] * 4, [0, 1, 2, 3], fl)
+    try:
+        b.set_chains_per_cta(2)
+        assert b.config()[3:] == (2, 1)
+        torch.cuda.synchronize()
+        b.run(dp.data_ptr(), 3, dout.data_ptr())
+        b.wait()
+        got = dout.cpu().numpy()
+        refs = []
+        for p in range(4):
+            x, y = hks[p].locations()
+            refs.append(oracle.loglik_grad(dss[p].t, x, y, params[p], s=None, rows=True))
+            _close(got[p], *refs[p], f"remainder problem {p}")
+        bad = params.copy()
+        bad[1, 2] = -1.0  # tau_t < 0 for the second member of the group
+        dp.copy_(torch.from_numpy(bad))
+        b.run(dp.data_ptr(), 3, dout.data_ptr())
+        with pytest.raises(HawkesError):
+            b.wait()
+        got2 = dout.cpu().numpy()
+        assert np.all(np.isnan(got2[1]))
+        for p in (0, 2, 3):
+            _close(got2[p], *refs[p], f"valid problem {p} beside an invalid group member")
+    finally:
+        b.close()
+        for h in hks:
+            h.close()
+
+
+def test_chains_per_cta_arguments(problems):
+    """k must be 1, 2 or 4, and k > 1 needs the full space-time gradient."""
+    from paper_2407_11349_gb300.hawkes import HAWKES_LOGLIK_ONLY, HAWKES_SKIP_UNDERFLOW
+    torch, dss, params, hks, seeds, streams = problems
+    b = Batch(hks, seeds, streams, HAWKES_F32)
+    try:
+        for k in (0, 3, 5, 8):
+            with pytest.raises(HawkesError):
+                b.set_chains_per_cta(k)
+    finally:
+        b.close()
+    for fl in (HAWKES_BG_TIME, HAWKES_LOGLIK_ONLY, HAWKES_SKIP_UNDERFLOW):
+        b = Batch(hks, seeds, streams, HAWKES_F32 | fl)
+        try:
+            with pytest.raises(HawkesError):
+                b.set_chains_per_cta(2)
+            b.set_chains_per_cta(1)
+        finally:
+            b.close()

@@ -58,6 +58,10 @@ def _failing_worker(rank, world, port, out_path):
         status = "error: " + type(e).__name__
     with open(out_path, "w") as f:
         f.write(status)
+    # Leave without running the broken process group's destructors: gloo's
+    # teardown after a lost peer can abort the process, which is not what
+    # this test is about (the status above is).
+    os._exit(0)
 
 
 def test_row_bounds_partition():
