@@ -218,6 +218,48 @@ def bench_batch(ds_c3, steps, warmup):
                       "medians of alternating batched / sequential repeats"}
 
 
+def bench_batch_kc(workload, kcs, chunk=64, repeats=3):
+    """Whole batched steps (CUDA graph) at fixed chains per CTA: "c4" is the
+    30-chain batch of the benchmark (30 x N = 250,000 plus the 16 regional
+    subsets), "c2x4" four chains of the N = 100,000 workload (a small case
+    for profiling).  Sweep variant 0, item order 0, the given chunk length.
+    Returns {chains_per_cta: median ms per step}."""
+    import torch
+    from paper_2407_11349_gb300 import synth
+    from paper_2407_11349_gb300.hawkes import HAWKES_F32, Batch, Hawkes
+
+    if workload == "c4":
+        dss = [synth.config_dataset("c4")] * 30 + synth.regional_subsets(
+            synth.config_dataset("c3"), synth.regional_sizes(), seed=3)
+    else:
+        dss = [synth.config_dataset("c2")] * 4
+    P = len(dss)
+    stream = torch.cuda.current_stream()
+    hks = [Hawkes(torch.cuda.current_device(), stream.cuda_stream).load(d) for d in dss]
+    dp = torch.tensor(synth.chain_params(P, seed=3), dtype=torch.float64, device="cuda")
+    dout = torch.zeros((P, 7), dtype=torch.float64, device="cuda")
+    b = Batch(hks, [3] * P, list(range(P)), HAWKES_F32, stream.cuda_stream)
+    out = {}
+    for kc in kcs:
+        b.set_config(0, chunk, 0)
+        b.set_chains_per_cta(kc)
+        b.capture(dp.data_ptr(), dout.data_ptr())
+        ts = []
+        for k in range(repeats + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(dp.data_ptr(), k, dout.data_ptr())
+            e1.record(stream)
+            b.wait()
+            if k:
+                ts.append(e0.elapsed_time(e1))
+        out[kc] = statistics.median(ts)
+    b.close()
+    for h in hks:
+        h.close()
+    return out
+
+
 def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, ref_rounds=0,
               lite=False, flags=0, moves=0, train_from="last", progress=None):
     """Min bulk ESS per second of exact HMC vs surrogate HMC, same data, same
@@ -530,6 +572,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 30-chain batch measurement")
+    ap.add_argument("--batch-only", default=None, choices=["c4", "c2x4"],
+                    help="time only batched steps at the chains-per-CTA values of --batch-kc")
+    ap.add_argument("--batch-kc", default="1,2,4", help="with --batch-only: chains per CTA to time")
+    ap.add_argument("--batch-chunk", type=int, default=64, help="with --batch-only: chunk length")
     ap.add_argument("--hmc-cut-reference", type=int, default=6,
                     help="location draws per chain for the independent cut-posterior reference (0: off)")
     ap.add_argument("--hmc-only", action="store_true",
@@ -580,6 +626,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.batch_only:
+        torch.cuda.set_stream(torch.cuda.Stream())
+        r = bench_batch_kc(args.batch_only, [int(k) for k in args.batch_kc.split(",")], args.batch_chunk)
+        print(json.dumps({"batch_only": args.batch_only, "chunk": args.batch_chunk,
+                          "ms_per_step_by_chains_per_cta": r}))
+        return
     if args.mh_only:
         torch.cuda.set_stream(torch.cuda.Stream())
         r = bench_mh(args.mh_n, chains=args.mh_chains, warmup=args.mh_warmup, draws=args.mh_draws,
