@@ -32,6 +32,7 @@ def test_round_trip_replace_and_valid_json(hk, tmp_path):
     doc = json.load(open(path))  # the file is plain JSON
     assert set(doc) == {KEY, "other|batch|P=46"}
     assert doc[KEY]["variant"] == 3 and doc[KEY]["nvariants"] == hk.hawkes_sweep_variants()
+    assert doc[KEY]["kc"] == 1  # chains per CTA (batches only; 1 through this entry point)
     assert not os.path.exists(path + ".tmp")
 
 
@@ -45,9 +46,12 @@ def test_damaged_and_stale_lines_are_misses(hk, tmp_path):
                 f'"stale": {{"variant": 0, "chunk": 16, "order": 0, "ms": 1.0, "nvariants": {nv + 3}}},\n'
                 f'"big": {{"variant": 1e400, "chunk": 16, "order": 0, "ms": 1.0, "nvariants": {nv}}},\n'
                 f'"range": {{"variant": {nv}, "chunk": 16, "order": 0, "ms": 1.0, "nvariants": {nv}}},\n'
+                f'"badkc": {{"variant": 1, "chunk": 16, "order": 0, "ms": 1.0, "nvariants": {nv}, "kc": 0}},\n'
+                f'"kc2": {{"variant": 1, "chunk": 16, "order": 0, "ms": 2.0, "nvariants": {nv}, "kc": 2}},\n'
                 f'"good": {{"variant": 2, "chunk": 32, "order": 1, "ms": 9.5, "nvariants": {nv}}}\n'
                 '}\n')
-    for k in ("half", "stale", "big", "range"):
+    assert hk.hawkes_tune_cache_get(path, "kc2") == (1, 16, 0, pytest.approx(2.0))
+    for k in ("half", "stale", "big", "range", "badkc"):
         assert hk.hawkes_tune_cache_get(path, k) is None, k
     assert hk.hawkes_tune_cache_get(path, "good") == (2, 32, 1, pytest.approx(9.5))
     # a write rewrites the file with its valid entries only
