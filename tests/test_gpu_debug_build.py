@@ -3,7 +3,8 @@ for a memory checker) on the GPU.
 
 In a child process that loads lib/libhawkes_debug.so: every regular path
 (symmetric sweep, row windows, ties, Model 1, the time-only background, the
-FP64 path, a batch, the allocation-free entry point) runs with no check
+FP64 path, a batch, a batch with two chains per CTA, the allocation-free
+entry point) runs with no check
 firing and matches the oracle at the FP32-path tolerances; then one work item
 is overwritten to end one column tile past its row tile's causal triangle.
 That tile is still inside the padded arrays, so the planted item is memory
@@ -73,6 +74,23 @@ CHILD = textwrap.dedent('''
         hks[p].resample(7, p, 2)
         ref, rows = hks[p].loglik_rows(params[p], HAWKES_F32)
         close(got[p, 0], got[p, 1:], ref, rows, 1e-6, 1e-5, f"batch problem {p}")
+    b.close()
+
+    # two chains per CTA (the group kernel): two chains of one data set and
+    # one other problem
+    dss = [dss[0], dss[0], dss[2]]
+    hks = [Hawkes(0).load(d) for d in dss]
+    b = Batch(hks, [7] * 3, [0, 1, 2], HAWKES_F32)
+    b.set_chains_per_cta(2)
+    assert b.config()[3:] == (2, 1)
+    torch.cuda.synchronize()
+    b.run(dp.data_ptr(), 3, dout.data_ptr())
+    b.wait()
+    got = dout.cpu().numpy()
+    for p in range(3):
+        hks[p].resample(7, p, 3)
+        ref, rows = hks[p].loglik_rows(params[p], HAWKES_F32)
+        close(got[p, 0], got[p, 1:], ref, rows, 1e-6, 1e-5, f"group batch problem {p}")
     b.close()
 
     # the allocation-free entry point (work list built on the device)
