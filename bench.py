@@ -261,7 +261,8 @@ def bench_batch_kc(workload, kcs, chunk=64, repeats=3):
 
 
 def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, ref_rounds=0,
-              lite=False, flags=0, moves=0, train_from="last", progress=None):
+              lite=False, flags=0, moves=0, train_from="last", progress=None, checkpoint=None,
+              resume=None):
     """Min bulk ESS per second of exact HMC vs surrogate HMC, same data, same
     adapted step size and metric.  cut=True: locations resampled every
     iteration (the cut-posterior scheme); cut=False: locations held fixed,
@@ -278,7 +279,12 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     location draw.  train_from: "last" trains the network on the warmup's
     evaluations from its last slow adaptation window on, "fast" on every
     evaluation after the first fast window (15% of the warmup).  progress:
-    a file that receives each finished part as one JSON line."""
+    a file that receives each finished part as one JSON line.  checkpoint:
+    write the warmup's end state (chains, step sizes, metric, iteration,
+    sampler RNG) and the training sets to this file and return; resume:
+    start from such a file instead of running the warmup (a long run split
+    over two processes)."""
+    import pickle
     from paper_2407_11349_gb300 import diagnostics as dg
     from paper_2407_11349_gb300 import hmc, synth
     from paper_2407_11349_gb300.hawkes import MLP
@@ -297,14 +303,30 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     # feature: the exact log-likelihood at a fixed anchor (the starting
     # point) under that draw, the seventh input of the feature network
     a_f = eta0.copy() if cut else None
-    t0 = time.perf_counter()
-    last = ex.warmup(warmup, feature_anchor=a_f)
-    t_warm = time.perf_counter() - t0
-    n_warm_exact = tgt.n_exact
-    first = last if train_from == "last" else int(0.15 * warmup)
-    rec = ex.record[1 + first * (leapfrog + 1):]
-    X, Y = hmc.training_set(rec)
-    ex.record = None
+    if resume:
+        with open(resume, "rb") as f:
+            ck = pickle.load(f)
+        ex.set_state(ck["state"])
+        ex.record = None
+        t_warm, n_warm_exact = ck["t_warm"], ck["n_warm_exact"]
+        X, Y, feat = ck["X"], ck["Y"], ck["feat"]
+    else:
+        t0 = time.perf_counter()
+        last = ex.warmup(warmup, feature_anchor=a_f)
+        t_warm = time.perf_counter() - t0
+        n_warm_exact = tgt.n_exact
+        first = last if train_from == "last" else int(0.15 * warmup)
+        rec = ex.record[1 + first * (leapfrog + 1):]
+        X, Y = hmc.training_set(rec)
+        feat = hmc.training_set(rec, with_feature=True) if cut else None
+        ex.record = None
+        if checkpoint:
+            with open(checkpoint, "wb") as f:
+                pickle.dump({"state": ex.state(), "t_warm": t_warm, "n_warm_exact": n_warm_exact,
+                             "X": X, "Y": Y, "feat": feat}, f)
+            tgt.close()
+            return {"checkpoint": checkpoint, "warmup_s": t_warm, "warmup_exact_evals": n_warm_exact,
+                    "training_pairs": int(X.shape[0])}
     net = MLP(torch_device(), seed=2)
     t0 = time.perf_counter()
     net.set_data(X, Y)
@@ -314,7 +336,7 @@ def bench_hmc(n_events, cut=True, chains=4, leapfrog=10, warmup=300, draws=300, 
     field = hmc.SurrogateField(net, chains)
     net_f = field_f = None
     if cut:
-        Xf, Yf, Ff = hmc.training_set(rec, with_feature=True)
+        Xf, Yf, Ff = feat
         net_f = MLP(torch_device(), seed=2)
         net_f.set_data(Xf, Yf, Ff)
         loss_f = net_f.train(4000, batch=512, lr=1e-3, seed=3)
@@ -599,6 +621,10 @@ def main():
                          "its first fast window (fast)")
     ap.add_argument("--hmc-progress", default=None,
                     help="with --hmc-only: append each finished part to this file as a JSON line")
+    ap.add_argument("--hmc-checkpoint", default=None,
+                    help="with --hmc-only: save the warmup's end state and training sets here and stop")
+    ap.add_argument("--hmc-resume", default=None,
+                    help="with --hmc-only: start from a --hmc-checkpoint file instead of warming up")
     ap.add_argument("--hmc-chains", type=int, default=4)
     ap.add_argument("--hmc-warmup", type=int, default=300)
     ap.add_argument("--hmc-draws", type=int, default=300)
@@ -645,6 +671,7 @@ def main():
         r = bench_hmc(args.hmc_n, cut=not args.hmc_fixed, chains=args.hmc_chains, warmup=args.hmc_warmup,
                       draws=args.hmc_draws, lite=True, ref_rounds=args.hmc_ref_rounds,
                       moves=args.hmc_moves, train_from=args.hmc_train_from, progress=args.hmc_progress,
+                      checkpoint=args.hmc_checkpoint, resume=args.hmc_resume,
                       flags=HAWKES_SKIP_SPATIAL if args.hmc_spatial else HAWKES_SKIP_UNDERFLOW)
         print(json.dumps({"hmc_only": r}))
         return
