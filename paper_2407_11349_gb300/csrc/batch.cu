@@ -593,8 +593,14 @@ int hawkes_batch_set_chains_per_cta(hawkes_batch* b, int chains_per_cta) {
         return HAWKES_ERR_ARG;
     DeviceGuard g(b->device);
     HB_CUDA(cudaStreamSynchronize(b->stream));
+    const int prev = b->kc;
     b->kc = chains_per_cta;
-    return build_items(b, b->variant, b->chunk, b->order);
+    const int rc = build_items(b, b->variant, b->chunk, b->order);
+    if (rc != HAWKES_OK) {  // e.g. no memory for the group tiles: keep the previous setting
+        b->kc = prev;
+        (void)build_items(b, b->variant, b->chunk, b->order);
+    }
+    return rc;
 }
 
 int hawkes_batch_get_config(const hawkes_batch* b, int* variant, int* chunk, int* order,
