@@ -43,7 +43,7 @@ ALG_FP32_OPS_PER_PAIR = 19
 # selection.  The kernel needs none of those 4 (scales and masks are applied
 # per row or per tile, outside the pair loop) and forms the excitation
 # argument with one FMA, so 19 is the stricter count; both are reported.
-SURVEY_FP32_OPS_PER_PAIR = 24
+ESTIMATED_FP32_OPS_PER_PAIR = 24
 # log-likelihood only: the row moments SBr, SBt, SEt, SEq and the column
 # moments SBr, SBt are not formed (6 fewer)
 LL_FP32_OPS_PER_PAIR = 13
@@ -895,7 +895,7 @@ def main():
                          "kernel": f"k_sweep variant {variant} (FP32 pair sweep)",
                          "tuned_ms": [round(float(x), 3) for x in tune_ms],
                          "per_unit": f"{ALG_FP32_OPS_PER_PAIR} FP32 lane ops per unordered pair",
-                         "frac_at_24_ops_per_pair": SURVEY_FP32_OPS_PER_PAIR * pairs / sweep_avg_s / peak_ops,
+                         "frac_at_24_ops_per_pair": ESTIMATED_FP32_OPS_PER_PAIR * pairs / sweep_avg_s / peak_ops,
                          "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
                                         f"(sm_max_mhz, {pk_src})",
                          "launch_ms": 1000 * sweep_avg_s},
